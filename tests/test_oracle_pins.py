@@ -1,0 +1,475 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by the
+mathematics of the scheme (no GPU needed).
+
+Each test names the passage it pins and the kind of pin: a closed form, an
+exact moment recurrence, a conservation invariant, an independent brute-force
+implementation on a tiny domain, or a number printed in the paper.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_04455_gb300 import inputs
+from tests.conftest import read_golden
+
+CX = oracle.CX
+CY = oracle.CY
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+OPP = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+
+
+# ---------------------------------------------------------------------------
+# p8: parameter conventions against the paper's worked numbers
+# ---------------------------------------------------------------------------
+def test_da_k_and_tau_d_worked_numbers():
+    """Sec. IV.A (Fig. singleAB caption): R = 5, Da = 150 <-> k = 1 and
+    Da = 1.5 <-> k = 0.01; Appendix C: tau = 1 <-> D = 0.1666."""
+    g = read_golden("paper_worked_numbers.txt")
+    d = (g["gauss_tau"] - 0.5) / 3.0
+    assert abs(d - g["gauss_D"]) < 1e-4
+    assert inputs.tau_from_diffusivity(d) == pytest.approx(g["gauss_tau"],
+                                                           abs=1e-15)
+    for da, k in ((g["single_Da_a"], g["single_k_a"]),
+                  (g["single_Da_b"], g["single_k_b"])):
+        assert inputs.rate_from_da(da, d, g["single_R"]) == pytest.approx(
+            k, rel=1e-12)
+        assert inputs.da_from_rate(k, d, g["single_R"]) == pytest.approx(
+            da, rel=1e-12)
+    # Pe = u0 R / D round trip
+    assert inputs.diffusivity_from_pe(0.05, 8.0, 10.0) == pytest.approx(0.04)
+
+
+# ---------------------------------------------------------------------------
+# raster: Gauss circle counts and side-by-side split
+# ---------------------------------------------------------------------------
+def test_raster_gauss_circle_counts():
+    """Node solid iff (x-cx)^2+(y-cy)^2 <= R^2: an integer-centred disc of
+    radius r holds exactly the Gauss-circle count of nodes (OEIS A000328)."""
+    rows = read_golden("gauss_circle.txt")[1:]
+    for r_s, n_s in rows:
+        r = int(r_s)
+        fib = [[15.0, 14.0, float(r), 1.0, 0.0, -1.0]]
+        solid, kab, kbc = oracle.raster(31, 29, fib, 0.3, 0.7)
+        assert int(solid.sum()) == int(n_s)
+        assert np.all(kab[solid == 1] == 0.3) and np.all(kbc == 0.0)
+
+
+def test_raster_janus_and_relaxed_weight():
+    """Side-by-side fiber (Sec. II.C): A->B on the half (p-c).n >= 0, B->C on
+    the other; relaxed weight w gives w*k1 and (1-w)*k2 on every node."""
+    fib = [[15.0, 14.0, 8.0, 3.0, 0.0, -1.0]]     # split line x = 15
+    solid, kab, kbc = oracle.raster(31, 29, fib, 0.3, 0.7)
+    ys, xs = np.nonzero(solid)
+    assert np.all(kab[ys, xs][xs >= 15] == 0.3)
+    assert np.all(kbc[ys, xs][xs < 15] == 0.7)
+    assert np.all((kab[ys, xs] > 0) ^ (kbc[ys, xs] > 0))
+    # disc of 197 nodes, column x = 15 holds 17 of them, halves are 90 each
+    assert int((kab > 0).sum()) == 90 + 17 and int((kbc > 0).sum()) == 90
+    fib = [[15.0, 14.0, 8.0, 1.0, 0.0, 0.25]]
+    solid, kab, kbc = oracle.raster(31, 29, fib, 0.4, 0.8)
+    assert np.allclose(kab[solid == 1], 0.1) and np.allclose(
+        kbc[solid == 1], 0.6)
+
+
+# ---------------------------------------------------------------------------
+# p1: homogeneous first-order reaction (Appendix C, Eq. source_lbm)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k1,k2", [(0.01, 0.03), (0.2, 0.05), (1.0, 0.5)])
+def test_homogeneous_cascade_closed_form(k1, k2):
+    """Periodic, u = 0, every population reacts: the discrete law is
+    C_A(t) = (1-k1)^t, C_B(t) = k1/(k2-k1) [(1-k1)^t - (1-k2)^t],
+    C_C = 1 - C_A - C_B; with k1 = 1 A vanishes after one step
+    (Appendix C: 'decays to zero instantaneously')."""
+    nx, ny = 6, 5
+    solid = np.zeros((ny, nx), np.uint8)
+    z = np.zeros((ny, nx))
+    prob = oracle.ADRProblem(solid, np.full((ny, nx), k1),
+                             np.full((ny, nx), k2), z, z, [0.7] * 3,
+                             [0, 0, 0], flags=oracle.PX | oracle.PY |
+                             oracle.ALLPOP)
+    g = prob.init()
+    for t in range(1, 41):
+        prob.steps(g, 1)
+        c = prob.conc(g)
+        a = (1 - k1) ** t
+        b = k1 / (k2 - k1) * ((1 - k1) ** t - (1 - k2) ** t)
+        assert np.allclose(c[0], a, rtol=1e-12, atol=1e-15)
+        assert np.allclose(c[1], b, rtol=1e-12, atol=1e-16)
+        assert np.allclose(c[2], 1 - a - b, rtol=1e-12, atol=1e-15)
+    if k1 == 1.0:
+        g = prob.init()
+        prob.steps(g, 1)
+        # zero up to the rounding of sum_i w_i = 1
+        assert np.abs(prob.conc(g)[0]).max() < 1e-15
+
+
+def test_homogeneous_decay_vs_exponential_small_k():
+    """Appendix C: for small k the lattice law follows exp(-k t); the gap is
+    (1-k)^t / exp(-kt) = exp(t (ln(1-k) + k)) = 1 - t k^2/2 + ..."""
+    k, t = 0.01, 100
+    nx, ny = 4, 4
+    solid = np.zeros((ny, nx), np.uint8)
+    z = np.zeros((ny, nx))
+    prob = oracle.ADRProblem(solid, np.full((ny, nx), k), z, z, z, [1.0, 1.0],
+                             [0, 0], flags=oracle.PX | oracle.PY |
+                             oracle.ALLPOP)
+    g = prob.init()
+    prob.steps(g, t)
+    ca = prob.conc(g)[0, 0, 0]
+    assert abs(ca / math.exp(-k * t) - 1) < t * k * k / 2 * 1.05
+
+
+# ---------------------------------------------------------------------------
+# p2/p3: Gaussian hill (Appendix C)
+# ---------------------------------------------------------------------------
+def _gauss_problem(n, sigma0, tau, u):
+    solid = np.zeros((n, n), np.uint8)
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    x0 = y0 = n / 2
+    c = np.exp(-((x - x0) ** 2 + (y - y0) ** 2) / (2 * sigma0 ** 2))
+    ux = np.full((n, n), u[0])
+    uy = np.full((n, n), u[1])
+    z = np.zeros((n, n))
+    prob = oracle.ADRProblem(solid, z, z, ux, uy, [tau], [0.0],
+                             flags=oracle.PX | oracle.PY)
+    return prob, c, x, y
+
+
+def _moments(c, x, y):
+    m = c.sum()
+    mx, my = (c * x).sum() / m, (c * y).sum() / m
+    vx = (c * (x - mx) ** 2).sum() / m
+    vy = (c * (y - my) ** 2).sum() / m
+    return m, mx, my, vx, vy
+
+
+@pytest.mark.parametrize("tau", [1.0, 0.8, 1.3])
+def test_gaussian_moment_recurrence_no_flow(tau):
+    """u = 0, equilibrium start: mass is exact, the centroid stays, and with
+    w = 1/tau the per-axis variance obeys the exact lattice recurrence
+    var(T) = var(0) + 2 D T - (2/3)(1-w)(1-(1-w)^T)/w^2, D = (tau-1/2)/3
+    (Eq. Diffusion_LBM), derived from the BGK relaxation of the first and
+    second moments."""
+    prob, c0, x, y = _gauss_problem(128, 2.0, tau, (0.0, 0.0))
+    g = prob.init(c0[None])
+    m0, mx0, my0, vx0, vy0 = _moments(c0, x, y)
+    T = 60
+    prob.steps(g, T)
+    c = prob.conc(g)[0]
+    m, mx, my, vx, vy = _moments(c, x, y)
+    w = 1.0 / tau
+    d = (tau - 0.5) / 3.0
+    expect = vx0 + 2 * d * T - (2 / 3) * (1 - w) * (1 - (1 - w) ** T) / w**2
+    assert m == pytest.approx(m0, rel=1e-13)
+    assert mx == pytest.approx(mx0, abs=1e-10)
+    assert my == pytest.approx(my0, abs=1e-10)
+    assert vx == pytest.approx(expect, rel=1e-11)
+    assert vy == pytest.approx(expect, rel=1e-11)
+
+
+def test_gaussian_moment_recurrence_with_flow():
+    """tau = 1, uniform u = (0.1, 0.1) (Appendix C): the centroid moves by
+    exactly u per step and each variance grows by exactly 1/3 per step."""
+    prob, c0, x, y = _gauss_problem(128, 2.0, 1.0, (0.1, 0.1))
+    g = prob.init(c0[None])
+    m0, mx0, my0, vx0, vy0 = _moments(c0, x, y)
+    T = 50
+    prob.steps(g, T)
+    m, mx, my, vx, vy = _moments(prob.conc(g)[0], x, y)
+    assert m == pytest.approx(m0, rel=1e-13)
+    assert mx == pytest.approx(mx0 + 0.1 * T, abs=1e-10)
+    assert my == pytest.approx(my0 + 0.1 * T, abs=1e-10)
+    assert vx == pytest.approx(vx0 + T / 3, rel=1e-11)
+    assert vy == pytest.approx(vy0 + T / 3, rel=1e-11)
+
+
+@pytest.mark.parametrize("u,t", [((0.0, 0.0), 100), ((0.0, 0.0), 400),
+                                 ((0.1, 0.1), 50), ((0.1, 0.1), 100)])
+def test_gaussian_hill_vs_analytic_profile(u, t):
+    """Appendix C: 100x100, sigma0 = 1, tau = 1 (D = 1/6); the lattice profile
+    follows the continuum solution
+    C = s0^2/(s0^2+2Dt) exp(-(x-x0-ut)^2 / (2(s0^2+2Dt))) up to a small
+    shape difference (max error below 2% of the peak)."""
+    n = 100
+    prob, c0, x, y = _gauss_problem(n, 1.0, 1.0, u)
+    g = prob.init(c0[None])
+    prob.steps(g, t)
+    c = prob.conc(g)[0]
+    d = 1.0 / 6.0
+    s2 = 1.0 + 2 * d * t
+    # periodic images of the analytic hill
+    ana = np.zeros_like(c)
+    for ix in (-1, 0, 1):
+        for iy in (-1, 0, 1):
+            dx = x - n / 2 - u[0] * t + ix * n
+            dy = y - n / 2 - u[1] * t + iy * n
+            ana += (1.0 / s2) * np.exp(-(dx**2 + dy**2) / (2 * s2))
+    err = np.abs(c - ana).max() / ana.max()
+    assert err < 2e-2
+
+
+# ---------------------------------------------------------------------------
+# p4: flow lattice
+# ---------------------------------------------------------------------------
+def _shear_wave_amplitude(ny, tau, t, u_amp=1e-4):
+    nx = 2
+    solid = np.zeros((ny, nx), np.uint8)
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    kk = 2 * np.pi / ny
+    ux = u_amp * np.sin(kk * y)
+    f = oracle.flow_init_fields(solid, np.ones((ny, nx)), ux,
+                                np.zeros((ny, nx)))
+    oracle.flow_steps(f, solid, tau, 0.0, t, flags=oracle.PX | oracle.PY)
+    _, ux_t, _ = oracle.flow_moments(f, solid)
+    amp = 2 * (ux_t[:, 0] * np.sin(kk * y[:, 0])).sum() / ny
+    return amp / u_amp, kk
+
+
+def test_shear_wave_decay_rate_converges_second_order():
+    """Fully periodic shear wave u_x = U sin(k y): decays as exp(-nu k^2 t)
+    with nu = (tau - 1/2)/3 in the continuum limit; the lattice error of the
+    decay exponent shrinks by ~4x when the wavelength doubles."""
+    tau = 0.8
+    nu = (tau - 0.5) / 3.0
+    errs = []
+    for ny in (32, 64):
+        kk = 2 * np.pi / ny
+        t = int(round(0.5 / (nu * kk * kk)))   # decay to ~exp(-0.5)
+        a, kk = _shear_wave_amplitude(ny, tau, t)
+        rate = -math.log(a) / t
+        errs.append(abs(rate / (nu * kk * kk) - 1))
+    assert errs[0] < 2e-2
+    assert 3.0 < errs[0] / errs[1] < 5.0
+
+
+def test_flow_mass_conserved_closed_box_with_fiber():
+    """Periodic in x, walls in y, a fiber: halfway bounce-back and BGK keep
+    the total mass exactly (to rounding)."""
+    nx, ny = 40, 24
+    solid, _, _ = oracle.raster(nx, ny, [[20.3, 11.7, 4.0, 0, 0, -1]], 0, 0)
+    rho = np.ones((ny, nx))
+    y = np.arange(ny)[:, None] * np.ones((1, nx))
+    ux = 0.03 * np.sin(np.pi * (y + 0.5) / ny) * (solid == 0)
+    f = oracle.flow_init_fields(solid, rho, ux, np.zeros((ny, nx)))
+    m0 = f.sum()
+    oracle.flow_steps(f, solid, 0.8, 0.0, 500, flags=oracle.PX)
+    assert f.sum() == pytest.approx(m0, rel=1e-13)
+
+
+def test_empty_channel_poiseuille_profile():
+    """Inlet-outlet channel without fibers (velocity bounce-back inlet with
+    the parabola 4 u0 (y+1/2)(ny-1/2-y)/ny^2, pressure anti-bounce-back
+    outlet, halfway bounce-back walls):
+    * at steady state the mass flux sum_y rho u_x through every column equals
+      the imposed inflow sum_y u_in(y) (to the residual);
+    * the profile shape in the middle of the channel is the parabola, with a
+      lattice error that falls by 4x when ny doubles (second order)."""
+    tau, u0 = 0.8, 0.01
+    errs = []
+    for ny, steps in ((12, 8000), (24, 12000)):
+        nx = 6 * ny
+        solid = np.zeros((ny, nx), np.uint8)
+        rho, ux, uy, res = oracle.flow_run(solid, tau, u0, steps)
+        assert res < 1e-4
+        yy = np.arange(ny)
+        para = 4 * u0 * (yy + 0.5) * (ny - 0.5 - yy) / ny**2
+        q = (rho * ux).sum(axis=0)
+        assert np.abs(q / para.sum() - 1).max() < 1e-5
+        prof = ux[:, nx // 2]
+        errs.append(np.linalg.norm(prof / prof.sum() - para / para.sum())
+                    / np.linalg.norm(para / para.sum()))
+        assert np.abs(uy[:, nx // 4:3 * nx // 4]).max() < 1e-4 * u0
+    assert errs[1] < 1e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+# ---------------------------------------------------------------------------
+# p5/p6: invariants of the channel ADR lattice
+# ---------------------------------------------------------------------------
+def _small_channel(nx=64, ny=24, steps=300):
+    fib = [[20.2, 11.3, 4.0, 1, 0, -1], [38.7, 12.4, 4.0, 2, 0, -1],
+           [29.1, 4.9, 2.0, 3, 1.0, -1]]
+    solid, kab, kbc = oracle.raster(nx, ny, fib, 0.05, 0.08)
+    _, ux, uy, _ = oracle.flow_run(solid, 0.8, 0.05, steps)
+    return solid, kab, kbc, ux, uy
+
+
+def test_species_sum_invariant_cascade():
+    """Eq. (source_lbm): the sources of A, B and C on each link add to zero,
+    so with equal tau and the same anti-bounce-back inlet for every species
+    (test mode, C_w = 1, 0, 0) the field C_A+C_B+C_C equals, at every node
+    and step, that of one non-reacting species."""
+    solid, kab, kbc, ux, uy = _small_channel()
+    tau = 0.62
+    p3 = oracle.ADRProblem(solid, kab, kbc, ux, uy, [tau] * 3, [1, 0, 0],
+                           flags=oracle.INLET_ABB_ALL)
+    p1 = oracle.ADRProblem(solid, kab * 0, kbc * 0, ux, uy, [tau], [1.0],
+                           flags=oracle.INLET_ABB_ALL)
+    g3, g1 = p3.init(), p1.init()
+    for _ in range(4):
+        p3.steps(g3, 50)
+        p1.steps(g1, 50)
+        s = p3.conc(g3).sum(axis=0)
+        one = p1.conc(g1)[0]
+        assert np.allclose(s, one, rtol=1e-13, atol=1e-14)
+        assert p3.flux(g3).sum() == pytest.approx(p1.flux(g1)[0], rel=1e-12)
+    # and the reaction really happened
+    c = p3.conc(g3)
+    assert c[1].max() > 1e-3 and c[2].max() > 1e-4
+
+
+def test_no_reaction_no_product():
+    """k = 0: B and C start at zero and nothing produces them, so their
+    concentrations and outfluxes stay exactly zero."""
+    solid, kab, kbc, ux, uy = _small_channel()
+    p = oracle.ADRProblem(solid, kab * 0, kbc * 0, ux, uy, [0.62] * 3,
+                          [1, 0, 0])
+    out = p.run(200)
+    assert np.all(out["conc"][1:] == 0.0)
+    assert out["flux"][1] == 0.0 and out["flux"][2] == 0.0
+    assert out["flux"][0] > 0 and out["eps"] == 0.0
+
+
+def test_efficiency_definition():
+    """Eq. (A-B)."""
+    assert oracle.efficiency([3.0, 1.0, 0.0], 2) == pytest.approx(0.25)
+    assert oracle.efficiency([1.0, 1.0, 2.0], 3) == pytest.approx(0.5)
+
+
+def test_pe_trend_single_fiber():
+    """Sec. IV.A: the efficiency falls as Pe rises (shorter contact time),
+    checked on a small single-fiber channel near steady state."""
+    nx, ny, r = 96, 48, 5.0
+    solid, kab, kbc = oracle.raster(nx, ny, [[30.0, 24.0, r, 1, 0, -1]], 1, 0)
+    _, ux, uy, _ = oracle.flow_run(solid, 0.8, 0.05, 3000)
+    eps = []
+    for pe in (2.0, 10.0, 50.0):
+        d = inputs.diffusivity_from_pe(0.05, r, pe)
+        tau = inputs.tau_from_diffusivity(d)
+        k = inputs.rate_from_da(1.0, d, r)
+        p = oracle.ADRProblem(solid, kab * k, kbc, ux, uy, [tau, tau],
+                              [1, 0])
+        eps.append(p.run(3000)["eps"])
+    assert eps[0] > eps[1] > eps[2] > 0
+
+
+# ---------------------------------------------------------------------------
+# p7: brute force -- an independent pull-form implementation on tiny domains
+# ---------------------------------------------------------------------------
+def _pull_step(gb, solid, kab, kbc, ux, uy, tau, cin, ns):
+    """Naive pull-form ADR step written from the rules, batched over the
+    first axis: gb[b, s, y, x, i] (pre-collision) -> next pre-collision."""
+    nb = gb.shape[0]
+    ny, nx = solid.shape
+    out = np.zeros_like(gb)
+    gs = np.zeros_like(gb)
+    # collision + source at every fluid node
+    for y in range(ny):
+        for x in range(nx):
+            if solid[y, x]:
+                continue
+            c = gb[:, :, y, x, :].sum(axis=2)            # [b, s]
+            cu = CX * ux[y, x] + CY * uy[y, x]
+            uu = ux[y, x] ** 2 + uy[y, x] ** 2
+            e = W * (1 + 3 * cu + 4.5 * cu**2 - 1.5 * uu)  # [i]
+            for s in range(ns):
+                gi = gb[:, s, y, x, :]
+                gs[:, s, y, x, :] = gi + (c[:, s:s + 1] * e - gi) / tau[s]
+            for i in range(1, 9):
+                tx, ty = x + CX[i], y + CY[i]
+                if not (0 <= tx < nx and 0 <= ty < ny) or not solid[ty, tx]:
+                    continue
+                ra = kab[ty, tx] * W[i] * c[:, 0]
+                rb = kbc[ty, tx] * W[i] * c[:, 1] if ns >= 3 else 0.0
+                gs[:, 0, y, x, i] -= ra
+                if ns >= 2:
+                    gs[:, 1, y, x, i] += ra - rb
+                if ns >= 3:
+                    gs[:, 2, y, x, i] += rb
+    # pull streaming with boundary rules
+    for y in range(ny):
+        for x in range(nx):
+            if solid[y, x]:
+                continue
+            for s in range(ns):
+                cb = gs[:, s, y, x, :].sum(axis=1)
+                for i in range(9):
+                    sx, sy = x - CX[i], y - CY[i]
+                    o = OPP[i]
+                    if sx < 0:          # came in through the inlet
+                        if s == 0:
+                            v = -gs[:, s, y, x, o] + 2 * W[i] * cin[s]
+                        else:
+                            v = gs[:, s, y, x, o]
+                    elif sx >= nx:      # came in through the outlet
+                        v = -gs[:, s, y, x, o] + 2 * W[i] * cb
+                    elif sy < 0 or sy >= ny or solid[sy, sx]:
+                        v = gs[:, s, y, x, o]
+                    else:
+                        v = gs[:, s, sy, sx, i]
+                    out[:, s, y, x, i] = v
+    return out
+
+
+def _tiny_case(ns):
+    nx, ny = 9, 6
+    fib = [[3.2, 2.6, 1.2, 1, 0, -1], [6.1, 3.4, 1.0, 2, 0, -1]]
+    solid, kab, kbc = oracle.raster(nx, ny, fib, 0.15, 0.25)
+    rng = np.random.default_rng(7)
+    ux = 0.04 + 0.02 * rng.random((ny, nx))
+    uy = 0.02 * (rng.random((ny, nx)) - 0.5)
+    ux[solid == 1] = 0
+    uy[solid == 1] = 0
+    tau = [0.9, 0.7, 0.8][:ns]
+    cin = [1.0, 0.0, 0.0][:ns]
+    return solid, kab, kbc, ux, uy, tau, cin
+
+
+@pytest.mark.parametrize("ns", [2, 3])
+def test_one_step_matches_independent_pull_implementation(ns):
+    """Every link type (inlet, outlet, wall, corner, catalytic fiber of both
+    kinds, plain fluid) on a 9x6 lattice: one oracle step (push form) equals
+    the naive pull-form step on random states."""
+    solid, kab, kbc, ux, uy, tau, cin = _tiny_case(ns)
+    assert solid.sum() >= 4
+    ny, nx = solid.shape
+    rng = np.random.default_rng(1)
+    g = rng.random((ns, ny, nx, 9)) * (solid == 0)[None, :, :, None]
+    prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, tau, cin)
+    want = _pull_step(g[None].copy(), solid, kab, kbc, ux, uy, tau, cin,
+                      ns)[0]
+    got = prob.steps(g.copy(), 1)
+    assert np.allclose(got, want, rtol=0, atol=1e-14)
+
+
+def test_steady_state_matches_dense_linear_solve():
+    """The ADR step is affine in g (frozen u): g' = M g + b.  The steady state
+    solves (I - M) g = b exactly; the oracle's long run must converge to it,
+    and the steady efficiency follows from it."""
+    ns = 3
+    solid, kab, kbc, ux, uy, tau, cin = _tiny_case(ns)
+    ny, nx = solid.shape
+    fluid = (solid == 0)
+    idx = [(s, y, x, i) for s in range(ns) for y in range(ny)
+           for x in range(nx) if fluid[y, x] for i in range(9)]
+    n = len(idx)
+    basis = np.zeros((n + 1, ns, ny, nx, 9))
+    for j, (s, y, x, i) in enumerate(idx):
+        basis[j + 1, s, y, x, i] = 1.0
+    img = _pull_step(basis, solid, kab, kbc, ux, uy, tau, cin, ns)
+    flat = lambda a: np.array([a[s, y, x, i] for (s, y, x, i) in idx])
+    b = flat(img[0])
+    m = np.stack([flat(img[j + 1]) - b for j in range(n)], axis=1)
+    gss = np.linalg.solve(np.eye(n) - m, b)
+    prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, tau, cin)
+    out = prob.run(6000)
+    got = flat(out["g"])
+    assert np.abs(got - gss).max() < 1e-11
+    gfull = np.zeros((ns, ny, nx, 9))
+    for v, (s, y, x, i) in zip(gss, idx):
+        gfull[s, y, x, i] = v
+    eps_exact = oracle.efficiency(prob.flux(gfull), ns)
+    assert out["eps"] == pytest.approx(eps_exact, abs=1e-11)
+    assert 0 < eps_exact < 1
