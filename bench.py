@@ -1,0 +1,420 @@
+"""Throughput benchmark of the coupled ADR lattice (species MLUPS and the HBM
+roofline fraction of the fused 3-species stream-collide kernel).
+
+Workload: the large membrane lattice, 16384 x 4096 nodes (67.1M), 2000 seeded
+R = 8 fibers in four membranes with alternating A->B / B->C catalysts,
+Pe = 50, Da = 0.5, species A, B, C.  Set-up (untimed): raster, upload, flow
+(D2Q9 BGK, fixed step count).  One benchmark step = 100 ADR time steps of all
+three species, the last two of which also record the concentration change,
+followed by the outflux reduction and the efficiency read back to the host:
+one pass of the whole hot path.  The population state (14.5 GB in FP32) is
+far larger than L2, so no flush is needed between steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f16dev|f64]
+python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+Under torchrun each rank solves its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+CHUNK = 100          # ADR time steps per benchmark step
+SPECIES = 3
+METRIC = "species MLUPS (ADR, 3 species)"
+UNIT = "MLUPS"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lbm", choices=["lbm", "reference"])
+    ap.add_argument("--precision", default="f32",
+                    choices=["f32", "f16dev", "f64"])
+    ap.add_argument("--flow-steps", type=int, default=2000)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--nx", type=int, default=16384)
+    ap.add_argument("--ny", type=int, default=4096)
+    ap.add_argument("--fibers-per-band", type=int, default=500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _workload(a, seed=0):
+    from paper_2109_04455_gb300 import inputs
+    return inputs.large_membrane(seed=seed, nx=a.nx, ny=a.ny,
+                                 per_band=a.fibers_per_band)
+
+
+def _config(a, w):
+    return {"workload": f"{w.name}: {w.nx}x{w.ny} D2Q9 channel, "
+                        f"{w.fibers.shape[0]} R=8 fibers in 4 membranes, "
+                        f"species A,B,C, Pe={w.pe:g}, Da={w.da1:g}",
+            "nx": w.nx, "ny": w.ny, "species": SPECIES,
+            "precision": a.precision, "adr_steps_per_step": CHUNK,
+            "flow_steps": a.flow_steps,
+            "l2": "inputs larger than L2 (population state >> 129 MB)",
+            "parallelism": f"replica per GPU x{a.gpus}"}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _loop(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", "-i", str(self.index),
+                     f"--query-gpu={self.Q}", "--format=csv,noheader,nounits"],
+                    capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([c.strip() for c in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._loop, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if r and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, n in enumerate(names):
+                if len(r) > 3 + k and r[3 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2109_04455_gb300", "csrc")
+    for f in ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "kernels_f32.cu",
+              "kernels_f16dev.cu", "kernels_f64.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(precision: str, units_per_launch: int):
+    """DRAM bytes per launch of the ADR step kernel from the committed ncu
+    summary, scaled to this launch by fluid nodes; None if the kernel source
+    changed since the capture."""
+    path = os.path.join(ROOT, "profiles", f"adr_step_{precision}_ncu.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    with open(path) as fh:
+        for line in fh:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+    try:
+        if kv.get("kernel_source_hash") != _kernel_source_hash():
+            return None
+        per_unit = float(kv["dram_bytes_per_fluid_node"])
+        return per_unit * units_per_launch
+    except (KeyError, ValueError):
+        return None
+
+
+def _algorithmic_bytes(geom, w, precision):
+    """Bytes one ADR step launch must move: per fluid node 3 species x 9
+    populations read + written, the velocity (2 values) and the link word;
+    per solid node its link word; the rates of each catalytic link (two
+    doubles)."""
+    import numpy as np
+    import torch
+    es = {"f32": 4, "f16dev": 2, "f64": 8}[precision]
+    ue = 8 if precision == "f64" else 4
+    n_nodes = geom.nx_pad * geom.ny
+    n_solid = geom.n_solid + (geom.nx_pad - geom.nx) * geom.ny
+    n_fluid = n_nodes - n_solid
+    links = geom.ws[:4 * n_nodes].view(torch.int32).cpu().numpy().view(np.uint32)
+    fl = links[links != 0xFFFFFFFF]
+    ncat = 0
+    for j in range(8):
+        ncat += int(((fl >> (4 * j)) & 0xF == 3).sum())
+    per_fluid = SPECIES * 9 * 2 * es + 2 * ue + 4
+    total = n_fluid * per_fluid + n_solid * 4 + ncat * 16
+    return total, n_fluid, per_fluid
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+def _oracle_sample(w, steps, nxs=1024, nys=512, x0=1536):
+    """Crop of the workload (x in [x0, x0+nxs), y in [0, nys)) with the fibers
+    that touch it; returns a callable that runs ``steps`` oracle ADR steps
+    and the species-node updates it performs."""
+    import numpy as np
+
+    import oracle
+    fib = w.fibers.copy()
+    fib[:, 0] -= x0
+    keep = ((fib[:, 0] + fib[:, 2] >= 0) & (fib[:, 0] - fib[:, 2] < nxs) &
+            (fib[:, 1] + fib[:, 2] >= 0) & (fib[:, 1] - fib[:, 2] < nys))
+    fib = fib[keep]
+    solid, kab, kbc = oracle.raster(nxs, nys, fib, w.k1, w.k2)
+    _, ux, uy, _ = oracle.flow_run(solid, w.tau_flow, w.u0, 20)
+    prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, [w.tau_c] * SPECIES,
+                             list(w.c_in))
+    state = {"g": prob.init()}
+
+    def run():
+        prob.steps(state["g"], steps)
+    desc = (f"x in [{x0},{x0 + nxs}) x y in [0,{nys}) crop of the workload "
+            f"({int(keep.sum())} fibers), {SPECIES} species, {steps} ADR "
+            "steps per sample, FP64 oracle, 1 thread")
+    return run, SPECIES * nxs * nys * steps, desc
+
+
+def cpu_baseline(w, target_s=12.0):
+    run, units, desc = _oracle_sample(w, 5)
+    t = time.perf_counter()
+    run()
+    dt = time.perf_counter() - t
+    reps = max(1, int(target_s / max(dt, 1e-3)))
+    t = time.perf_counter()
+    for _ in range(reps):
+        run()
+    dt = time.perf_counter() - t
+    return {"value": units * reps / dt / 1e6, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": f"{desc}; {reps} samples, {dt:.1f} s"}
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = _workload(a)
+    run, units, desc = _oracle_sample(w, 5)
+    for _ in range(a.warmup):
+        run()
+    t = time.perf_counter()
+    for _ in range(a.steps):
+        run()
+    dt = time.perf_counter() - t
+    value = units * a.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value,
+            "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": _config(a, w),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def run_gpu(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2109_04455_gb300 import lbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    prec = lbm.PRECISIONS[a.precision]
+    w = _workload(a, seed=rank)
+
+    # ---- set-up (untimed): raster, upload, flow
+    geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload(dev)
+    stream = torch.cuda.current_stream()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+        enable_timing=True)
+    f0.record(stream)
+    u, finfo = lbm.lbm_flow_solve(geom, w.tau_flow, w.u0, a.flow_steps,
+                                  precision=lbm.LBM_F64 if prec == lbm.LBM_F64
+                                  else lbm.LBM_F32)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    flow_ms = f0.elapsed_time(f1)
+    flow_mlups = w.nx * w.ny * a.flow_steps / (flow_ms * 1e-3) / 1e6
+
+    prm = lbm.adr_params(SPECIES, w.tau_c, w.c_in, precision=prec)
+    solver = lbm.ADRSolver(geom, prm, u).init()
+
+    def bench_step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        solver.run(CHUNK - 2, check=False)
+        if evs is not None:
+            evs[1].record(stream)
+        return solver.run(2)
+
+    for _ in range(a.warmup):
+        info = bench_step()
+
+    # ---- timed region
+    n_ev = a.steps
+    ev_plain = [(torch.cuda.Event(enable_timing=True),
+                 torch.cuda.Event(enable_timing=True)) for _ in range(n_ev)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+        enable_timing=True)
+    gpu_index = dev.index
+    try:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            gpu_index = int(vis.split(",")[dev.index])
+    except ValueError:
+        pass
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_index) as clk:
+        t0.record(stream)
+        for k in range(a.steps):
+            info = bench_step(ev_plain[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed = t0.elapsed_time(t1) * 1e-3
+    plain_s = sum(e0.elapsed_time(e1) for e0, e1 in ev_plain) * 1e-3
+    launches_per_step = CHUNK + 2   # steps + partial-sum reduce + flux
+    if world > 1:
+        tt = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+
+    updates = SPECIES * w.nx * w.ny * CHUNK * a.steps
+    value = updates * world / elapsed / 1e6
+
+    # roofline of the dominant kernel (the fused ADR step)
+    alg_bytes, n_fluid, per_fluid = _algorithmic_bytes(geom, w, a.precision)
+    step_launch_s = plain_s / ((CHUNK - 2) * a.steps)
+    achieved = alg_bytes / step_launch_s / 1e9
+    peak, peak_kind = _peak_hbm()
+    traffic = _ncu_traffic(a.precision, n_fluid)
+
+    # ---- end to end through the public API with host buffers
+    ws_host = torch.empty(geom.ws.numel(), dtype=torch.uint8, pin_memory=True)
+    ws_host.copy_(geom.ws)
+    u_host = torch.empty(u.shape, dtype=u.dtype, pin_memory=True)
+    u_host.copy_(u)
+    h2d = ws_host.numel() + u_host.numel() * u_host.element_size()
+    d2h = 16 * 8
+    e2e_steps = max(1, a.e2e_steps)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+        enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        geom.ws.copy_(ws_host, non_blocking=True)
+        u.copy_(u_host, non_blocking=True)
+        bench_step()          # ends with the D2H read of flux / eps
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) * 1e-3
+    if world > 1:
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = SPECIES * w.nx * w.ny * CHUNK * e2e_steps * world / e2e_s / 1e6
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": elapsed / a.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f32": "f32", "f16dev": "f16-storage/f32-compute",
+                      "f64": "f64"}[a.precision],
+            "data": "synthetic (seeded fiber geometry)",
+            "config": _config(a, w),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic,
+                         "peak_kind": f"{peak_kind} (copy bandwidth)",
+                         "kernel": f"adr_kernel<{a.precision},3 species,step>",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "bytes_per_fluid_node": per_fluid,
+                         "fluid_nodes": n_fluid,
+                         "avg_launch_ms": step_launch_s * 1e3},
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * a.steps,
+            "clocks": clk.summary(),
+            "flow": {"mlups": flow_mlups, "steps": a.flow_steps,
+                     "residual": finfo["residual"]},
+            "eps": info["eps"], "adr_residual": info["residual"],
+        }
+        if not a.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * liblbm -- GB300 (sm_103a) lattice-Boltzmann solver for flow and
+ * advection-diffusion-reaction (ADR) through a 2D cross-section of catalytic
+ * fibrous membranes (Sitaru & Gekle, "Analytical and computational study of
+ * cascade reaction processes in catalytic fibrous membranes", arXiv
+ * 2109.04455).
+ *
+ * Pipeline (Sec. III.A, the hybrid one-way scheme): geometry -> steady flow
+ * (D2Q9 BGK) -> frozen velocity u -> ADR lattices for species A, B, C with
+ * first-order surface reactions A->B (rate k1) and B->C (rate k2) -> outflow
+ * fluxes -> efficiency (Eq. A-B).
+ *
+ * Conventions common to every entry point:
+ *  - Every call returns an lbm_status; on failure lbm_last_error() gives a
+ *    message (per calling thread).  Nothing aborts or traps.
+ *  - The library never allocates device memory.  The caller allocates every
+ *    device buffer, sized by the *_ws_bytes queries, and keeps it alive while
+ *    a geometry or solver object refers to it.  Device pointers are at least
+ *    256-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls that report numbers
+ *    (lbm_flow_solve, lbm_adr_run with info, lbm_adr_solve) synchronise it.
+ *  - Lattice: nodes (x, y), 0 <= x < nx (flow direction), 0 <= y < ny.  Device
+ *    fields are row-major [ny][nx_pad], x contiguous, nx_pad = nx rounded up
+ *    to a multiple of 32; multi-component fields put the component first
+ *    ([2][ny][nx_pad] for u, [nspecies][ny][nx_pad] for concentrations).
+ *    Columns x >= nx are padding (value 0 on output).
+ *  - Inlet at x = -1/2, outlet at x = nx - 1/2, halfway bounce-back walls at
+ *    y = -1/2 and y = ny - 1/2.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = 1,         /* bad argument (null pointer, size, tau <= 1/2) */
+  LBM_ENOMEM = 2,         /* a caller-provided workspace is too small      */
+  LBM_ECUDA = 3,          /* a CUDA runtime call or kernel launch failed   */
+  LBM_ENOTCONVERGED = 4,  /* max_steps reached above the tolerance          */
+  LBM_EUNSTABLE = 5       /* NaN or Inf met in the residual / flux sums     */
+} lbm_status;
+
+typedef enum {
+  LBM_F64 = 0,    /* populations stored and computed in double              */
+  LBM_F32 = 1,    /* populations stored and computed in float               */
+  LBM_F16DEV = 2  /* populations stored in half as g - w_i*c_ref,s (c_ref =
+                     inlet concentration of the species), computed in float */
+} lbm_precision;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *lbm_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Geometry (Sec. II.B/II.C: fibers are infinitely long cylinders, i.e.     */
+/* discs in the 2D cross-section).                                          */
+/* ------------------------------------------------------------------------ */
+typedef struct lbm_geometry lbm_geometry;
+
+/* Rasterise fibers on an nx x ny lattice (host work, no GPU needed).
+ * fibers: host, nfibers rows of 6 doubles: cx, cy, r, cat, janus_angle,
+ *   weight.  cat 0 inert, 1 catalyses A->B (rate k1), 2 catalyses B->C
+ *   (rate k2), 3 side-by-side fiber (Sec. II.C): A->B on the half where
+ *   (p - c).(cos a, sin a) >= 0, B->C on the other half.  weight >= 0 on a
+ *   catalytic fiber replaces that by the relaxed assignment k_AB = weight*k1,
+ *   k_BC = (1 - weight)*k2 on all its nodes; use -1 for none.
+ * A node is solid iff (x - cx)^2 + (y - cy)^2 <= r^2 for some fiber; the first
+ * such fiber in list order sets its rates.  Needs nx >= 4 and
+ * 1 <= ny <= 65535 (one grid row of blocks per lattice row).
+ * On success *out owns host memory; free it with lbm_geometry_destroy. */
+lbm_status lbm_geometry_create(int32_t nx, int32_t ny, const double *fibers,
+                               int32_t nfibers, double k1, double k2,
+                               lbm_geometry **out);
+void lbm_geometry_destroy(lbm_geometry *g);
+
+/* nx_pad and the number of solid nodes. Either pointer may be NULL. */
+lbm_status lbm_geometry_info(const lbm_geometry *g, int32_t *nx_pad,
+                             int64_t *n_solid);
+
+/* Host copies of the raster: solid (ny*nx bytes, 1 = solid) and the per-node
+ * rates k_AB, k_BC (ny*nx doubles each, row-major, unpadded).  Any output
+ * pointer may be NULL. */
+lbm_status lbm_geometry_fields(const lbm_geometry *g, uint8_t *solid,
+                               double *kab, double *kbc);
+
+/* Device bytes lbm_geometry_upload needs. */
+size_t lbm_geometry_ws_bytes(const lbm_geometry *g);
+
+/* Copy the link table and the rate fields into the caller's device buffer
+ * dev_ws (>= lbm_geometry_ws_bytes bytes) on `stream` and wait for the copy.
+ * The geometry keeps (borrows) dev_ws for the solver calls below. */
+lbm_status lbm_geometry_upload(lbm_geometry *g, void *dev_ws, size_t ws_bytes,
+                               void *stream);
+
+/* Solve calls report: */
+typedef struct {
+  int64_t steps;     /* time steps taken since initialisation              */
+  double residual;   /* per-step relative L1 change at the last check      */
+  int32_t converged; /* 1 if residual < tol at the last check              */
+  double flux[3];    /* outfluxes N_A, N_B, N_C (ADR only)                  */
+  double eps;        /* efficiency (ADR only; 0 if undefined)               */
+} lbm_solve_info;
+
+/* ------------------------------------------------------------------------ */
+/* Flow: D2Q9 BGK, standing in for the paper's D3Q19 MRT flow (Sec.         */
+/* III.A.1, Eq. LBE).  Pull streaming with halfway bounce-back on fibers and */
+/* walls, velocity bounce-back inlet with the parabola                       */
+/*   u_in(y) = 4 u0 (y + 1/2)(ny - 1/2 - y)/ny^2   (rho_w = 1)               */
+/* and pressure anti-bounce-back outlet (rho_w = 1, u_w = the boundary       */
+/* node's velocity).  Starts from rho = 1, u = (u_in(y), 0).                 */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  double tau;          /* relaxation time (> 1/2)                           */
+  double u0;           /* inflow centreline velocity                        */
+  int64_t max_steps;   /* step cap (or exact count when tol <= 0)           */
+  double tol;          /* stop when residual < tol; <= 0: run max_steps     */
+  int32_t check_every; /* steps per convergence check (>= 2)                */
+  int32_t precision;   /* LBM_F64 or LBM_F32 (LBM_F16DEV runs as LBM_F32)   */
+} lbm_flow_params;
+
+size_t lbm_flow_ws_bytes(const lbm_geometry *g, int32_t precision);
+
+/* Run the flow and write u (device, [2][ny][nx_pad], double for LBM_F64 else
+ * float; 0 on solid and padding nodes) at the final step.  residual =
+ * sum|u(t)-u(t-1)|_1 / sum|u(t)|_1.  Returns LBM_ENOTCONVERGED (with u and
+ * info filled) when tol > 0 is not reached within max_steps. */
+lbm_status lbm_flow_solve(const lbm_geometry *g, const lbm_flow_params *p,
+                          void *f_ws, size_t f_ws_bytes, void *u_out,
+                          void *stream, lbm_solve_info *info);
+
+/* ------------------------------------------------------------------------ */
+/* ADR lattices (Sec. III.A.2-3): per species s, BGK (Eq. BGK) towards the   */
+/* second-order equilibrium with the frozen u, tau_s = 3 D_s + 1/2 (Eq.      */
+/* Diffusion_LBM), C_s = sum_i g_{s,i}.  Dawson source (Eq. source_lbm) only */
+/* on populations that stream into a catalytic solid node n:                 */
+/*   Q_A = -k_AB(n) w_i C_A, Q_B = +k_AB(n) w_i C_A - k_BC(n) w_i C_B,       */
+/*   Q_C = +k_BC(n) w_i C_B   (pre-collision C at the fluid node).           */
+/* Boundaries (Eq. BC): fibers and walls bounce-back; inlet anti-bounce-back */
+/* g = -g* + 2 w_i c_in for species A (bounce-back for B, C unless           */
+/* LBM_ADR_INLET_ABB_ALL); outlet anti-bounce-back with C_w = sum_j g*_j of   */
+/* the boundary node.  All species advance in one kernel pass per step.      */
+/* Start: C_A = 1 on fluid nodes, B = C = 0, g = g^eq.                       */
+/* Outflux (Sec. III.A.3): N_s = (1/ny) sum_y sum_i c_ix g*_{s,i}(x_plane,y) */
+/* of the post-collision populations, accumulated in double.                  */
+/* ------------------------------------------------------------------------ */
+#define LBM_ADR_INLET_ABB_ALL 1 /* anti-bounce-back inlet for every species */
+
+typedef struct {
+  int32_t nspecies;    /* 1 (A only), 2 (A->B) or 3 (A->B->C)               */
+  int32_t precision;   /* lbm_precision                                     */
+  double tau[3];       /* relaxation time per species (> 1/2)               */
+  double c_in[3];      /* inlet concentration per species (A: 1)            */
+  int64_t max_steps;   /* lbm_adr_solve: step cap (exact count if tol <= 0) */
+  double tol;          /* lbm_adr_solve: stop when residual < tol           */
+  int32_t check_every; /* lbm_adr_solve: steps per check (>= 2)             */
+  int32_t x_plane;     /* flux plane; < 0 selects nx - 3                    */
+  int32_t flags;       /* LBM_ADR_* bits                                    */
+} lbm_adr_params;
+
+/* Device bytes of the ADR workspace (two population buffers, the
+ * concentration scratch and the reduction partials). */
+size_t lbm_adr_ws_bytes(const lbm_geometry *g, const lbm_adr_params *p);
+
+typedef struct lbm_adr_solver lbm_adr_solver;
+
+/* Bind a solver to an uploaded geometry, the device velocity u ([2][ny]
+ * [nx_pad], double for LBM_F64 else float) and a workspace ws.  Host object
+ * only; nothing runs on the GPU. */
+lbm_status lbm_adr_create(const lbm_geometry *g, const lbm_adr_params *p,
+                          const void *u, void *ws, size_t ws_bytes,
+                          lbm_adr_solver **out);
+void lbm_adr_destroy(lbm_adr_solver *s);
+
+/* Set the initial state (C_A = 1, others 0, g = g^eq) and steps = 0. */
+lbm_status lbm_adr_init(lbm_adr_solver *s, void *stream);
+
+/* Advance nsteps time steps.  info == NULL: enqueue only (no host sync).
+ * info != NULL (nsteps >= 2): the last two steps also record C and the
+ * residual, the outflux on the plane is reduced, the stream is synchronised
+ * and info is filled; LBM_EUNSTABLE if a sum is not finite. */
+lbm_status lbm_adr_run(lbm_adr_solver *s, int64_t nsteps, void *stream,
+                       lbm_solve_info *info);
+
+/* Copy C_s at the last checked step (device, [nspecies][ny][nx_pad], double
+ * for LBM_F64 else float) to conc_out. */
+lbm_status lbm_adr_conc(lbm_adr_solver *s, void *conc_out, void *stream);
+
+/* One-shot solve: create, init, run in chunks of check_every until
+ * residual < tol (or exactly max_steps if tol <= 0), copy C to conc_out
+ * (may be NULL), destroy.  LBM_ENOTCONVERGED if tol was not reached. */
+lbm_status lbm_adr_solve(const lbm_geometry *g, const lbm_adr_params *p,
+                         const void *u, void *ws, size_t ws_bytes,
+                         void *conc_out, void *stream, lbm_solve_info *info);
+
+/* Eq. (A-B): eps = N_B/(N_A+N_B) for nspecies 2, N_C/(N_A+N_B+N_C) for 3.
+ * Host arithmetic only.  LBM_EINVAL for other nspecies or a zero sum. */
+lbm_status lbm_efficiency(const double *flux, int32_t nspecies, double *eps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

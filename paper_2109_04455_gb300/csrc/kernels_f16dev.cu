@@ -1,0 +1,11 @@
+// Kernel instantiations for PrecF16Dev.
+#include "lbm_launch_impl.cuh"
+
+namespace lbm {
+template cudaError_t launch_adr<PrecF16Dev>(int, int, const AdrArgs &, dim3,
+                                            cudaStream_t);
+template cudaError_t launch_adr_flux<PrecF16Dev>(int, const void *,
+                                                 const uint32_t *, long long,
+                                                 int, int, int, const double *,
+                                                 double *, cudaStream_t);
+}  // namespace lbm

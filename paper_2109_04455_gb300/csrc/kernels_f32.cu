@@ -1,0 +1,13 @@
+// Kernel instantiations for PrecF32.
+#include "lbm_launch_impl.cuh"
+
+namespace lbm {
+template cudaError_t launch_adr<PrecF32>(int, int, const AdrArgs &, dim3,
+                                            cudaStream_t);
+template cudaError_t launch_adr_flux<PrecF32>(int, const void *,
+                                                 const uint32_t *, long long,
+                                                 int, int, int, const double *,
+                                                 double *, cudaStream_t);
+template cudaError_t launch_flow<PrecF32>(int, const FlowArgs &, dim3,
+                                             cudaStream_t);
+}  // namespace lbm

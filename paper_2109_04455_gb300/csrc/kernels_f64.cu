@@ -1,0 +1,13 @@
+// Kernel instantiations for PrecF64.
+#include "lbm_launch_impl.cuh"
+
+namespace lbm {
+template cudaError_t launch_adr<PrecF64>(int, int, const AdrArgs &, dim3,
+                                            cudaStream_t);
+template cudaError_t launch_adr_flux<PrecF64>(int, const void *,
+                                                 const uint32_t *, long long,
+                                                 int, int, int, const double *,
+                                                 double *, cudaStream_t);
+template cudaError_t launch_flow<PrecF64>(int, const FlowArgs &, dim3,
+                                             cudaStream_t);
+}  // namespace lbm

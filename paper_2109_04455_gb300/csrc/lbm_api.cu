@@ -1,0 +1,563 @@
+// Host side of the liblbm C ABI (include/lbm.h): argument checks, workspace
+// carving, the solve loops and their convergence checks.  All device memory
+// is the caller's; this file only launches kernels on the caller's stream.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+cudaError_t launch_reduce(int k, const double *partials, long long nb,
+                          double *out, cudaStream_t st) {
+  const dim3 block(kReduceThreads);
+  switch (k) {
+    case 2: reduce_partials_kernel<2><<<1, block, 0, st>>>(partials, nb, out); break;
+    case 4: reduce_partials_kernel<4><<<1, block, 0, st>>>(partials, nb, out); break;
+    case 6: reduce_partials_kernel<6><<<1, block, 0, st>>>(partials, nb, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+namespace {
+
+inline cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+inline long long plane_of(const lbm_geometry *g) {
+  return static_cast<long long>(g->nx_pad) * g->ny;
+}
+
+inline dim3 lattice_grid(const lbm_geometry *g) {
+  return dim3(static_cast<unsigned>((g->nx_pad + kBlockX - 1) / kBlockX),
+              static_cast<unsigned>(g->ny));
+}
+
+inline long long grid_blocks(const lbm_geometry *g) {
+  const dim3 gr = lattice_grid(g);
+  return static_cast<long long>(gr.x) * gr.y;
+}
+
+inline bool aligned256(const void *p) {
+  return (reinterpret_cast<uintptr_t>(p) & 255u) == 0;
+}
+
+lbm_status cuda_fail(const char *where, cudaError_t e) {
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return LBM_ECUDA;
+}
+
+size_t store_bytes(int prec) {
+  return prec == LBM_F64 ? 8 : (prec == LBM_F32 ? 4 : 2);
+}
+size_t compute_bytes(int prec) { return prec == LBM_F64 ? 8 : 4; }
+
+// Make the device that owns `p` current for this thread (the caller's
+// buffers decide where the work runs); rejects host memory.
+lbm_status bind_device(const void *p, const char *where) {
+  cudaPointerAttributes at{};
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) return cuda_fail(where, e);
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
+    set_error(std::string(where) + ": buffer is not device memory");
+    return LBM_EINVAL;
+  }
+  int cur = -1;
+  e = cudaGetDevice(&cur);
+  if (e == cudaSuccess && cur != at.device) e = cudaSetDevice(at.device);
+  if (e != cudaSuccess) return cuda_fail(where, e);
+  return LBM_OK;
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" const char *lbm_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------------------
+// geometry upload
+// ---------------------------------------------------------------------------
+extern "C" size_t lbm_geometry_ws_bytes(const lbm_geometry *g) {
+  if (!g) return 0;
+  const size_t p = static_cast<size_t>(plane_of(g));
+  return align256(4 * p) + 2 * align256(8 * p);
+}
+
+extern "C" lbm_status lbm_geometry_upload(lbm_geometry *g, void *dev_ws,
+                                          size_t ws_bytes, void *stream) {
+  if (!g || !dev_ws) {
+    set_error("lbm_geometry_upload: NULL argument");
+    return LBM_EINVAL;
+  }
+  if (!aligned256(dev_ws)) {
+    set_error("lbm_geometry_upload: workspace not 256-byte aligned");
+    return LBM_EINVAL;
+  }
+  const size_t need = lbm_geometry_ws_bytes(g);
+  if (ws_bytes < need) {
+    set_error("lbm_geometry_upload: workspace too small (" +
+              std::to_string(ws_bytes) + " < " + std::to_string(need) + ")");
+    return LBM_ENOMEM;
+  }
+  if (lbm_status bs = bind_device(dev_ws, "lbm_geometry_upload")) return bs;
+  const size_t p = static_cast<size_t>(plane_of(g));
+  char *b = static_cast<char *>(dev_ws);
+  uint32_t *d_links = reinterpret_cast<uint32_t *>(b);
+  double *d_kab = reinterpret_cast<double *>(b + align256(4 * p));
+  double *d_kbc = reinterpret_cast<double *>(b + align256(4 * p) + align256(8 * p));
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(d_links, g->links.data(), 4 * p,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_kab, g->kab.data(), 8 * p, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_kbc, g->kbc.data(), 8 * p, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail("lbm_geometry_upload", e);
+  g->d_links = d_links;
+  g->d_kab = d_kab;
+  g->d_kbc = d_kbc;
+  g->uploaded = true;
+  return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// flow
+// ---------------------------------------------------------------------------
+static int flow_prec(int32_t precision) {
+  return precision == LBM_F64 ? LBM_F64 : LBM_F32;
+}
+
+extern "C" size_t lbm_flow_ws_bytes(const lbm_geometry *g, int32_t precision) {
+  if (!g) return 0;
+  const size_t p = static_cast<size_t>(plane_of(g));
+  const size_t es = store_bytes(flow_prec(precision));
+  return 2 * align256(9 * p * es) +
+         align256(static_cast<size_t>(grid_blocks(g)) * 2 * 8) + align256(64 * 8);
+}
+
+static cudaError_t flow_launch(int prec, int mode, const FlowArgs &a, dim3 grid,
+                               cudaStream_t st) {
+  return prec == LBM_F64 ? launch_flow<PrecF64>(mode, a, grid, st)
+                         : launch_flow<PrecF32>(mode, a, grid, st);
+}
+
+extern "C" lbm_status lbm_flow_solve(const lbm_geometry *g,
+                                     const lbm_flow_params *p, void *f_ws,
+                                     size_t f_ws_bytes, void *u_out,
+                                     void *stream, lbm_solve_info *info) {
+  if (!g || !p || !f_ws || !u_out) {
+    set_error("lbm_flow_solve: NULL argument");
+    return LBM_EINVAL;
+  }
+  if (!g->uploaded) {
+    set_error("lbm_flow_solve: geometry not uploaded");
+    return LBM_EINVAL;
+  }
+  if (!(p->tau > 0.5) || p->max_steps < 2 || p->check_every < 2 ||
+      !std::isfinite(p->u0)) {
+    set_error("lbm_flow_solve: need tau > 1/2, max_steps >= 2, check_every >= 2");
+    return LBM_EINVAL;
+  }
+  if (!aligned256(f_ws) || !aligned256(u_out)) {
+    set_error("lbm_flow_solve: device buffers must be 256-byte aligned");
+    return LBM_EINVAL;
+  }
+  const int prec = flow_prec(p->precision);
+  const size_t need = lbm_flow_ws_bytes(g, p->precision);
+  if (f_ws_bytes < need) {
+    set_error("lbm_flow_solve: workspace too small");
+    return LBM_ENOMEM;
+  }
+  if (lbm_status bs = bind_device(f_ws, "lbm_flow_solve")) return bs;
+  const size_t pl = static_cast<size_t>(plane_of(g));
+  const size_t bufb = align256(9 * pl * store_bytes(prec));
+  char *b = static_cast<char *>(f_ws);
+  void *buf[2] = {b, b + bufb};
+  double *partials = reinterpret_cast<double *>(b + 2 * bufb);
+  double *result = reinterpret_cast<double *>(
+      b + 2 * bufb + align256(static_cast<size_t>(grid_blocks(g)) * 16));
+  cudaStream_t st = as_stream(stream);
+  const dim3 grid = lattice_grid(g);
+
+  FlowArgs a{};
+  a.links = g->d_links;
+  a.u = u_out;
+  a.partials = partials;
+  a.plane = plane_of(g);
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.nx_pad = g->nx_pad;
+  a.omega = 1.0 / p->tau;
+  a.u0 = p->u0;
+
+  cudaError_t e = cudaMemsetAsync(b, 0, 2 * bufb, st);
+  if (e != cudaSuccess) return cuda_fail("lbm_flow_solve", e);
+  a.src = nullptr;
+  a.dst = buf[0];
+  e = flow_launch(prec, kFlowInit, a, grid, st);
+  if (e != cudaSuccess) return cuda_fail("lbm_flow_solve(init)", e);
+  int cur = 0;
+  int64_t steps = 0;
+  double residual = INFINITY;
+  bool converged = false;
+
+  auto step = [&](int mode) -> cudaError_t {
+    a.src = buf[cur];
+    a.dst = buf[cur ^ 1];
+    cur ^= 1;
+    ++steps;
+    return flow_launch(prec, mode, a, grid, st);
+  };
+  // n steps, the last two writing u and the residual sums
+  auto chunk = [&](int64_t n) -> lbm_status {
+    for (int64_t k = 0; k < n - 2; ++k) {
+      cudaError_t e2 = step(kFlowStep);
+      if (e2 != cudaSuccess) return cuda_fail("lbm_flow_solve(step)", e2);
+    }
+    cudaError_t e2 = step(kFlowU);
+    if (e2 == cudaSuccess) e2 = step(kFlowCheck);
+    if (e2 == cudaSuccess) e2 = launch_reduce(2, partials, grid_blocks(g), result, st);
+    double h[2] = {0, 0};
+    if (e2 == cudaSuccess)
+      e2 = cudaMemcpyAsync(h, result, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) return cuda_fail("lbm_flow_solve(check)", e2);
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) {
+      residual = NAN;
+      set_error("lbm_flow_solve: non-finite velocity");
+      return LBM_EUNSTABLE;
+    }
+    residual = h[1] > 0 ? h[0] / h[1] : 0.0;
+    return LBM_OK;
+  };
+
+  lbm_status s = LBM_OK;
+  if (p->tol <= 0) {
+    s = chunk(p->max_steps);
+  } else {
+    while (s == LBM_OK) {
+      const int64_t left = p->max_steps - steps;
+      const int64_t n = left < p->check_every ? left : p->check_every;
+      s = chunk(n < 2 ? 2 : n);
+      if (s != LBM_OK) break;
+      if (residual < p->tol) {
+        converged = true;
+        break;
+      }
+      if (steps >= p->max_steps) {
+        set_error("lbm_flow_solve: not converged within max_steps");
+        s = LBM_ENOTCONVERGED;
+      }
+    }
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->steps = steps;
+    info->residual = residual;
+    info->converged = converged ? 1 : 0;
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// ADR
+// ---------------------------------------------------------------------------
+struct lbm_adr_solver {
+  const lbm_geometry *g = nullptr;
+  lbm_adr_params p{};
+  AdrArgs a{};
+  void *buf[2] = {nullptr, nullptr};
+  void *cprev = nullptr;
+  double *partials = nullptr;
+  double *result = nullptr;
+  int cur = 0;
+  int64_t steps = 0;
+  bool has_check = false;
+  dim3 grid;
+  long long nb = 0;
+};
+
+struct AdrLayout {
+  size_t buf, cprev, partials, result, total;
+};
+
+static AdrLayout adr_layout(const lbm_geometry *g, const lbm_adr_params *p) {
+  const size_t pl = static_cast<size_t>(plane_of(g));
+  const size_t ns = static_cast<size_t>(p->nspecies);
+  AdrLayout l{};
+  l.buf = align256(ns * 9 * pl * store_bytes(p->precision));
+  l.cprev = align256(ns * pl * compute_bytes(p->precision));
+  l.partials = align256(static_cast<size_t>(grid_blocks(g)) * 2 * ns * 8);
+  l.result = align256(64 * 8);
+  l.total = 2 * l.buf + l.cprev + l.partials + l.result;
+  return l;
+}
+
+static bool adr_params_ok(const lbm_adr_params *p) {
+  if (p->nspecies < 1 || p->nspecies > 3) return false;
+  if (p->precision < LBM_F64 || p->precision > LBM_F16DEV) return false;
+  for (int s = 0; s < p->nspecies; ++s)
+    if (!(p->tau[s] > 0.5) || !std::isfinite(p->c_in[s])) return false;
+  return true;
+}
+
+extern "C" size_t lbm_adr_ws_bytes(const lbm_geometry *g,
+                                   const lbm_adr_params *p) {
+  if (!g || !p || !adr_params_ok(p)) return 0;
+  return adr_layout(g, p).total;
+}
+
+static cudaError_t adr_launch(int prec, int ns, int mode, const AdrArgs &a,
+                              dim3 grid, cudaStream_t st) {
+  switch (prec) {
+    case LBM_F64: return launch_adr<PrecF64>(ns, mode, a, grid, st);
+    case LBM_F32: return launch_adr<PrecF32>(ns, mode, a, grid, st);
+    default: return launch_adr<PrecF16Dev>(ns, mode, a, grid, st);
+  }
+}
+
+static cudaError_t adr_flux_launch(const lbm_adr_solver *s, cudaStream_t st) {
+  const lbm_geometry *g = s->g;
+  int xp = s->p.x_plane < 0 ? g->nx - 3 : s->p.x_plane;
+  const void *cur = s->buf[s->cur];
+  double *out = s->result + 8;
+  const int ns = s->p.nspecies;
+  switch (s->p.precision) {
+    case LBM_F64:
+      return launch_adr_flux<PrecF64>(ns, cur, g->d_links, plane_of(g), g->nx_pad,
+                                      g->ny, xp, s->a.cref, out, st);
+    case LBM_F32:
+      return launch_adr_flux<PrecF32>(ns, cur, g->d_links, plane_of(g), g->nx_pad,
+                                      g->ny, xp, s->a.cref, out, st);
+    default:
+      return launch_adr_flux<PrecF16Dev>(ns, cur, g->d_links, plane_of(g),
+                                         g->nx_pad, g->ny, xp, s->a.cref, out, st);
+  }
+}
+
+extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
+                                     const lbm_adr_params *p, const void *u,
+                                     void *ws, size_t ws_bytes,
+                                     lbm_adr_solver **out) {
+  if (!out) {
+    set_error("lbm_adr_create: out is NULL");
+    return LBM_EINVAL;
+  }
+  *out = nullptr;
+  if (!g || !p || !u || !ws) {
+    set_error("lbm_adr_create: NULL argument");
+    return LBM_EINVAL;
+  }
+  if (!g->uploaded) {
+    set_error("lbm_adr_create: geometry not uploaded");
+    return LBM_EINVAL;
+  }
+  if (!adr_params_ok(p)) {
+    set_error("lbm_adr_create: need 1..3 species, a known precision, tau > 1/2");
+    return LBM_EINVAL;
+  }
+  const int xp = p->x_plane < 0 ? g->nx - 3 : p->x_plane;
+  if (xp < 0 || xp >= g->nx) {
+    set_error("lbm_adr_create: flux plane outside the lattice");
+    return LBM_EINVAL;
+  }
+  if (!aligned256(u) || !aligned256(ws)) {
+    set_error("lbm_adr_create: device buffers must be 256-byte aligned");
+    return LBM_EINVAL;
+  }
+  const AdrLayout l = adr_layout(g, p);
+  if (ws_bytes < l.total) {
+    set_error("lbm_adr_create: workspace too small (" + std::to_string(ws_bytes) +
+              " < " + std::to_string(l.total) + ")");
+    return LBM_ENOMEM;
+  }
+  if (lbm_status bs = bind_device(ws, "lbm_adr_create")) return bs;
+  lbm_adr_solver *s = new (std::nothrow) lbm_adr_solver;
+  if (!s) {
+    set_error("lbm_adr_create: host allocation failed");
+    return LBM_ENOMEM;
+  }
+  char *b = static_cast<char *>(ws);
+  s->g = g;
+  s->p = *p;
+  s->buf[0] = b;
+  s->buf[1] = b + l.buf;
+  s->cprev = b + 2 * l.buf;
+  s->partials = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev);
+  s->result = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials);
+  s->grid = lattice_grid(g);
+  s->nb = grid_blocks(g);
+  AdrArgs &a = s->a;
+  a.links = g->d_links;
+  a.kab = g->d_kab;
+  a.kbc = g->d_kbc;
+  a.u = u;
+  a.cprev = s->cprev;
+  a.partials = s->partials;
+  a.plane = plane_of(g);
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.nx_pad = g->nx_pad;
+  a.abb_all = (p->flags & LBM_ADR_INLET_ABB_ALL) ? 1 : 0;
+  for (int k = 0; k < 3; ++k) {
+    const bool on = k < p->nspecies;
+    a.omega[k] = on ? 1.0 / p->tau[k] : 0.0;
+    a.cin[k] = on ? p->c_in[k] : 0.0;
+    a.cref[k] = (on && p->precision == LBM_F16DEV) ? p->c_in[k] : 0.0;
+  }
+  *out = s;
+  return LBM_OK;
+}
+
+extern "C" void lbm_adr_destroy(lbm_adr_solver *s) { delete s; }
+
+extern "C" lbm_status lbm_adr_init(lbm_adr_solver *s, void *stream) {
+  if (!s) {
+    set_error("lbm_adr_init: solver is NULL");
+    return LBM_EINVAL;
+  }
+  if (lbm_status bs = bind_device(s->buf[0], "lbm_adr_init")) return bs;
+  cudaStream_t st = as_stream(stream);
+  const AdrLayout l = adr_layout(s->g, &s->p);
+  cudaError_t e = cudaMemsetAsync(s->buf[0], 0, 2 * l.buf + l.cprev, st);
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_init", e);
+  AdrArgs a = s->a;
+  a.src = nullptr;
+  a.dst = s->buf[0];
+  e = adr_launch(s->p.precision, s->p.nspecies, kAdrInit, a, s->grid, st);
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_init(kernel)", e);
+  s->cur = 0;
+  s->steps = 0;
+  s->has_check = false;
+  return LBM_OK;
+}
+
+static cudaError_t adr_step(lbm_adr_solver *s, int mode, cudaStream_t st) {
+  AdrArgs a = s->a;
+  a.src = s->buf[s->cur];
+  a.dst = s->buf[s->cur ^ 1];
+  s->cur ^= 1;
+  ++s->steps;
+  return adr_launch(s->p.precision, s->p.nspecies, mode, a, s->grid, st);
+}
+
+extern "C" lbm_status lbm_adr_run(lbm_adr_solver *s, int64_t nsteps,
+                                  void *stream, lbm_solve_info *info) {
+  if (!s || nsteps < 0 || (info && nsteps < 2)) {
+    set_error("lbm_adr_run: need a solver, nsteps >= 0 (>= 2 with info)");
+    return LBM_EINVAL;
+  }
+  if (lbm_status bs = bind_device(s->buf[0], "lbm_adr_run")) return bs;
+  cudaStream_t st = as_stream(stream);
+  const int ns = s->p.nspecies;
+  const int64_t plain = info ? nsteps - 2 : nsteps;
+  for (int64_t k = 0; k < plain; ++k) {
+    cudaError_t e = adr_step(s, kAdrStep, st);
+    if (e != cudaSuccess) return cuda_fail("lbm_adr_run(step)", e);
+  }
+  if (!info) return LBM_OK;
+  cudaError_t e = adr_step(s, kAdrCheck, st);
+  if (e == cudaSuccess) e = adr_step(s, kAdrCheck, st);
+  if (e == cudaSuccess) e = launch_reduce(2 * ns, s->partials, s->nb, s->result, st);
+  if (e == cudaSuccess) e = adr_flux_launch(s, st);
+  double h[16] = {0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h, s->result, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_run(check)", e);
+  s->has_check = true;
+  std::memset(info, 0, sizeof(*info));
+  info->steps = s->steps;
+  bool finite = true;
+  double r = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    const double num = h[2 * k], den = h[2 * k + 1];
+    finite = finite && std::isfinite(num) && std::isfinite(den) &&
+             std::isfinite(h[8 + k]);
+    if (den > 0) r = std::fmax(r, num / den);
+    info->flux[k] = h[8 + k];
+  }
+  info->residual = finite ? r : NAN;
+  info->converged = (finite && s->p.tol > 0 && r < s->p.tol) ? 1 : 0;
+  if (ns >= 2) {
+    double eps = 0.0;
+    if (lbm_efficiency(info->flux, ns, &eps) == LBM_OK) info->eps = eps;
+  }
+  if (!finite) {
+    set_error("lbm_adr_run: non-finite concentration or flux");
+    return LBM_EUNSTABLE;
+  }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_adr_conc(lbm_adr_solver *s, void *conc_out,
+                                   void *stream) {
+  if (!s || !conc_out) {
+    set_error("lbm_adr_conc: NULL argument");
+    return LBM_EINVAL;
+  }
+  if (!s->has_check) {
+    set_error("lbm_adr_conc: no checked step yet (run with info first)");
+    return LBM_EINVAL;
+  }
+  if (lbm_status bs = bind_device(conc_out, "lbm_adr_conc")) return bs;
+  const size_t bytes = static_cast<size_t>(s->p.nspecies) *
+                       static_cast<size_t>(plane_of(s->g)) *
+                       compute_bytes(s->p.precision);
+  cudaError_t e = cudaMemcpyAsync(conc_out, s->cprev, bytes,
+                                  cudaMemcpyDeviceToDevice, as_stream(stream));
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_conc", e);
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_adr_solve(const lbm_geometry *g,
+                                    const lbm_adr_params *p, const void *u,
+                                    void *ws, size_t ws_bytes, void *conc_out,
+                                    void *stream, lbm_solve_info *info) {
+  if (!p || p->max_steps < 2 || (p->tol > 0 && p->check_every < 2)) {
+    set_error("lbm_adr_solve: need max_steps >= 2 and check_every >= 2");
+    return LBM_EINVAL;
+  }
+  lbm_adr_solver *s = nullptr;
+  lbm_status st = lbm_adr_create(g, p, u, ws, ws_bytes, &s);
+  if (st != LBM_OK) return st;
+  st = lbm_adr_init(s, stream);
+  lbm_solve_info loc{};
+  if (st == LBM_OK) {
+    if (p->tol <= 0) {
+      st = lbm_adr_run(s, p->max_steps, stream, &loc);
+    } else {
+      while (true) {
+        const int64_t left = p->max_steps - s->steps;
+        const int64_t n = left < p->check_every ? left : p->check_every;
+        st = lbm_adr_run(s, n < 2 ? 2 : n, stream, &loc);
+        if (st != LBM_OK || loc.converged) break;
+        if (s->steps >= p->max_steps) {
+          set_error("lbm_adr_solve: not converged within max_steps");
+          st = LBM_ENOTCONVERGED;
+          break;
+        }
+      }
+    }
+  }
+  if ((st == LBM_OK || st == LBM_ENOTCONVERGED) && conc_out) {
+    lbm_status c = lbm_adr_conc(s, conc_out, stream);
+    if (c == LBM_OK) {
+      cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+      if (e != cudaSuccess) c = cuda_fail("lbm_adr_solve", e);
+    }
+    if (c != LBM_OK) st = c;
+  }
+  if (info) *info = loc;
+  lbm_adr_destroy(s);
+  return st;
+}

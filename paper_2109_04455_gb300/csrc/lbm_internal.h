@@ -1,0 +1,50 @@
+// Internal definitions shared by the host geometry builder and the CUDA
+// translation unit of liblbm.  Not part of the public C ABI (include/lbm.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// Link word of a fluid node: nibble j-1 (j = 1..8) classifies the neighbour
+// x + c_j along D2Q9 direction j.  A solid or padding node has the word
+// kSolidNode and is never updated.
+enum LinkType : uint32_t {
+  kFluid = 0,   // fluid lattice node: plain streaming
+  kWall = 1,    // channel wall beyond y = -1/2 or y = ny - 1/2
+  kInert = 2,   // fiber node without a rate: bounce-back
+  kCat = 3,     // fiber node with a rate: bounce-back + Dawson source
+  kInlet = 4,   // beyond x = -1/2
+  kOutlet = 5,  // beyond x = nx - 1/2
+};
+constexpr uint32_t kSolidNode = 0xFFFFFFFFu;
+
+// D2Q9, textbook numbering: c_0 = 0; c_1..4 = E, N, W, S; c_5..8 = NE, NW,
+// SW, SE.
+constexpr int kCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+constexpr int kCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+inline int64_t pad32(int64_t n) { return (n + 31) / 32 * 32; }
+inline size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+void set_error(const std::string &msg);
+
+}  // namespace lbm
+
+struct lbm_geometry {
+  int32_t nx = 0, ny = 0, nx_pad = 0;
+  int64_t n_solid = 0;
+  std::vector<uint8_t> solid;     // [ny][nx]
+  std::vector<double> kab, kbc;   // [ny][nx_pad]
+  std::vector<uint32_t> links;    // [ny][nx_pad]
+  // device copies (borrowed from the caller's workspace after upload)
+  const uint32_t *d_links = nullptr;
+  const double *d_kab = nullptr;
+  const double *d_kbc = nullptr;
+  bool uploaded = false;
+};

@@ -1,0 +1,312 @@
+"""ctypes binding of ``liblbm.so`` (C ABI in ``include/lbm.h``).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  PyTorch provides device memory (``torch.empty`` on ``cuda``)
+and streams; the library itself never allocates device memory.  If the
+library has not been built, :func:`load` raises -- there is no other path.
+
+Function names follow the C ABI (``lbm_geometry_create`` ...); the small
+classes below only own the handles and the torch buffers they borrow.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTCONVERGED, \
+    LBM_EUNSTABLE = range(6)
+LBM_F64, LBM_F32, LBM_F16DEV = range(3)
+LBM_ADR_INLET_ABB_ALL = 1
+PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16dev": LBM_F16DEV}
+
+_STATUS = {LBM_EINVAL: "EINVAL", LBM_ENOMEM: "ENOMEM", LBM_ECUDA: "ECUDA",
+           LBM_ENOTCONVERGED: "ENOTCONVERGED", LBM_EUNSTABLE: "EUNSTABLE"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class lbm_solve_info(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("residual", ctypes.c_double),
+                ("converged", ctypes.c_int32),
+                ("flux", ctypes.c_double * 3), ("eps", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(steps=int(self.steps), residual=float(self.residual),
+                    converged=bool(self.converged),
+                    flux=[float(v) for v in self.flux], eps=float(self.eps))
+
+
+class lbm_flow_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("u0", ctypes.c_double),
+                ("max_steps", ctypes.c_int64), ("tol", ctypes.c_double),
+                ("check_every", ctypes.c_int32),
+                ("precision", ctypes.c_int32)]
+
+
+class lbm_adr_params(ctypes.Structure):
+    _fields_ = [("nspecies", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("tau", ctypes.c_double * 3), ("c_in", ctypes.c_double * 3),
+                ("max_steps", ctypes.c_int64), ("tol", ctypes.c_double),
+                ("check_every", ctypes.c_int32), ("x_plane", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+# name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "lbm_last_error": (ctypes.c_char_p, []),
+    "lbm_geometry_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P,
+                                           ctypes.c_int32, ctypes.c_double,
+                                           ctypes.c_double, _P]),
+    "lbm_geometry_destroy": (None, [_P]),
+    "lbm_geometry_info": (ctypes.c_int, [_P, _P, _P]),
+    "lbm_geometry_fields": (ctypes.c_int, [_P, _P, _P, _P]),
+    "lbm_geometry_ws_bytes": (ctypes.c_size_t, [_P]),
+    "lbm_geometry_upload": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
+    "lbm_flow_ws_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),
+    "lbm_flow_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, _P, _P,
+                                      _P]),
+    "lbm_adr_ws_bytes": (ctypes.c_size_t, [_P, _P]),
+    "lbm_adr_create": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "lbm_adr_destroy": (None, [_P]),
+    "lbm_adr_init": (ctypes.c_int, [_P, _P]),
+    "lbm_adr_run": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
+    "lbm_adr_conc": (ctypes.c_int, [_P, _P, _P]),
+    "lbm_adr_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_size_t, _P, _P,
+                                     _P]),
+    "lbm_efficiency": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+}
+
+_lib = None
+
+
+def load():
+    """Open liblbm.so (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != LBM_OK:
+        raise LBMError(status, load().lbm_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _device_bytes(nbytes: int, device="cuda"):
+    import torch
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def lbm_efficiency(flux, nspecies: int) -> float:
+    f = (ctypes.c_double * 3)(*[float(v) for v in list(flux)[:3]] +
+                              [0.0] * (3 - min(3, len(list(flux)))))
+    eps = ctypes.c_double()
+    _check(load().lbm_efficiency(f, nspecies, ctypes.byref(eps)))
+    return eps.value
+
+
+# ---------------------------------------------------------------------------
+# geometry
+# ---------------------------------------------------------------------------
+class Geometry:
+    """Host raster (lbm_geometry_create) plus its device copy."""
+
+    def __init__(self, nx: int, ny: int, fibers, k1: float, k2: float):
+        lib = load()
+        fib = np.ascontiguousarray(np.asarray(fibers, dtype=np.float64)
+                                   .reshape(-1, 6))
+        self._fib = fib
+        h = ctypes.c_void_p()
+        _check(lib.lbm_geometry_create(nx, ny, fib.ctypes.data_as(_P),
+                                       fib.shape[0], k1, k2, ctypes.byref(h)))
+        self.handle = h
+        self.nx, self.ny = nx, ny
+        pad = ctypes.c_int32()
+        nsol = ctypes.c_int64()
+        _check(lib.lbm_geometry_info(h, ctypes.byref(pad), ctypes.byref(nsol)))
+        self.nx_pad = pad.value
+        self.n_solid = nsol.value
+        self.ws = None
+
+    def fields(self):
+        """Host solid mask (uint8 [ny, nx]) and rates k_AB, k_BC."""
+        solid = np.zeros((self.ny, self.nx), np.uint8)
+        kab = np.zeros((self.ny, self.nx))
+        kbc = np.zeros((self.ny, self.nx))
+        _check(load().lbm_geometry_fields(self.handle,
+                                          solid.ctypes.data_as(_P),
+                                          kab.ctypes.data_as(_P),
+                                          kbc.ctypes.data_as(_P)))
+        return solid, kab, kbc
+
+    def ws_bytes(self) -> int:
+        return int(load().lbm_geometry_ws_bytes(self.handle))
+
+    def upload(self, device="cuda", stream=None):
+        self.ws = _device_bytes(self.ws_bytes(), device)
+        _check(load().lbm_geometry_upload(self.handle,
+                                          ctypes.c_void_p(self.ws.data_ptr()),
+                                          self.ws.numel(),
+                                          _stream_ptr(stream)))
+        return self
+
+    def close(self):
+        if self.handle:
+            load().lbm_geometry_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _field_dtype(precision: int):
+    import torch
+    return torch.float64 if precision == LBM_F64 else torch.float32
+
+
+def lbm_flow_solve(geom: Geometry, tau: float, u0: float, max_steps: int,
+                   tol: float = 0.0, check_every: int = 100,
+                   precision: int = LBM_F64, stream=None, u_out=None,
+                   raise_not_converged: bool = False):
+    """Run the flow lattice; returns (u [2, ny, nx_pad] on the device, info).
+    LBM_ENOTCONVERGED is reported in info (converged = False) unless
+    ``raise_not_converged``."""
+    import torch
+    lib = load()
+    p = lbm_flow_params(tau, u0, int(max_steps), tol, int(check_every),
+                        precision)
+    ws = _device_bytes(lib.lbm_flow_ws_bytes(geom.handle, precision),
+                       geom.ws.device)
+    if u_out is None:
+        u_out = torch.zeros((2, geom.ny, geom.nx_pad),
+                            dtype=_field_dtype(precision),
+                            device=geom.ws.device)
+    info = lbm_solve_info()
+    st = lib.lbm_flow_solve(geom.handle, ctypes.byref(p),
+                            ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                            ctypes.c_void_p(u_out.data_ptr()),
+                            _stream_ptr(stream), ctypes.byref(info))
+    if st != LBM_OK and not (st == LBM_ENOTCONVERGED and
+                             not raise_not_converged):
+        _check(st)
+    return u_out, info.as_dict()
+
+
+def adr_params(nspecies: int, tau, c_in=(1.0, 0.0, 0.0),
+               precision: int = LBM_F64, max_steps: int = 0, tol: float = 0.0,
+               check_every: int = 100, x_plane: int = -1,
+               flags: int = 0) -> lbm_adr_params:
+    taus = list(tau) if hasattr(tau, "__len__") else [tau] * nspecies
+    taus = (taus + [1.0] * 3)[:3]
+    cin = (list(c_in) + [0.0] * 3)[:3]
+    return lbm_adr_params(nspecies, precision, (ctypes.c_double * 3)(*taus),
+                          (ctypes.c_double * 3)(*cin), int(max_steps), tol,
+                          int(check_every), x_plane, flags)
+
+
+class ADRSolver:
+    """lbm_adr_create / init / run / conc over a torch workspace."""
+
+    def __init__(self, geom: Geometry, params: lbm_adr_params, u):
+        lib = load()
+        self.geom, self.params, self.u = geom, params, u
+        self.ws = _device_bytes(lib.lbm_adr_ws_bytes(geom.handle,
+                                                     ctypes.byref(params)),
+                                geom.ws.device)
+        h = ctypes.c_void_p()
+        _check(lib.lbm_adr_create(geom.handle, ctypes.byref(params),
+                                  ctypes.c_void_p(u.data_ptr()),
+                                  ctypes.c_void_p(self.ws.data_ptr()),
+                                  self.ws.numel(), ctypes.byref(h)))
+        self.handle = h
+
+    def init(self, stream=None):
+        _check(load().lbm_adr_init(self.handle, _stream_ptr(stream)))
+        return self
+
+    def run(self, nsteps: int, stream=None, check: bool = True):
+        """Advance nsteps; with check=True returns the info dict (syncs)."""
+        if not check:
+            _check(load().lbm_adr_run(self.handle, int(nsteps),
+                                      _stream_ptr(stream), None))
+            return None
+        info = lbm_solve_info()
+        _check(load().lbm_adr_run(self.handle, int(nsteps),
+                                  _stream_ptr(stream), ctypes.byref(info)))
+        return info.as_dict()
+
+    def conc(self, stream=None):
+        import torch
+        c = torch.empty((self.params.nspecies, self.geom.ny,
+                         self.geom.nx_pad),
+                        dtype=_field_dtype(self.params.precision),
+                        device=self.geom.ws.device)
+        _check(load().lbm_adr_conc(self.handle, ctypes.c_void_p(c.data_ptr()),
+                                   _stream_ptr(stream)))
+        return c
+
+    def close(self):
+        if self.handle:
+            load().lbm_adr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbm_adr_solve(geom: Geometry, params: lbm_adr_params, u, stream=None,
+                  want_conc: bool = True,
+                  raise_not_converged: bool = False):
+    """One-shot ADR solve; returns (conc or None, info)."""
+    import torch
+    lib = load()
+    ws = _device_bytes(lib.lbm_adr_ws_bytes(geom.handle, ctypes.byref(params)),
+                       geom.ws.device)
+    conc = None
+    if want_conc:
+        conc = torch.empty((params.nspecies, geom.ny, geom.nx_pad),
+                           dtype=_field_dtype(params.precision),
+                           device=geom.ws.device)
+    info = lbm_solve_info()
+    st = lib.lbm_adr_solve(geom.handle, ctypes.byref(params),
+                           ctypes.c_void_p(u.data_ptr()),
+                           ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                           ctypes.c_void_p(conc.data_ptr()) if want_conc
+                           else None, _stream_ptr(stream), ctypes.byref(info))
+    if st != LBM_OK and not (st == LBM_ENOTCONVERGED and
+                             not raise_not_converged):
+        _check(st)
+    return conc, info.as_dict()

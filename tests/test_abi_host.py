@@ -1,0 +1,112 @@
+"""Host-side checks of liblbm (no GPU): the library loads and exports every
+entry point the header declares, the host raster matches the oracle's
+bit for bit, argument errors come back as status codes, and the host-only
+efficiency call follows Eq. (A-B)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2109_04455_gb300 import inputs, lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2109_04455_gb300 import _build
+    _build.build()
+    return lbm.load()
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"\b(lbm_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert "lbm_adr_run" in names and "lbm_flow_solve" in names
+    for n in names:
+        assert hasattr(lib, n), f"liblbm.so does not export {n}"
+    # the binding wraps each of them under the same name
+    for n in names:
+        assert n in lbm._SIGS, f"binding misses {n}"
+
+
+@pytest.mark.parametrize("make", [
+    lambda: inputs.single_fiber(),
+    lambda: inputs.two_membrane_cascade(seed=1),
+    lambda: inputs.sweep_instance(5),
+    lambda: inputs.sweep_instance(42),
+])
+def test_host_raster_matches_oracle(lib, make):
+    w = make()
+    fib = w.fibers.copy()
+    if w.name.startswith("cascade"):
+        fib[::7, 5] = 0.3   # a few relaxed catalyst weights
+    g = lbm.Geometry(w.nx, w.ny, fib, w.k1, w.k2)
+    s, a, b = g.fields()
+    so, ao, bo = oracle.raster(w.nx, w.ny, fib, w.k1, w.k2)
+    assert np.array_equal(s, so)
+    assert np.array_equal(a, ao)
+    assert np.array_equal(b, bo)
+    assert g.n_solid == int(so.sum())
+    assert g.nx_pad % 32 == 0 and g.nx_pad >= w.nx
+
+
+def test_argument_errors_are_status_codes(lib):
+    h = ctypes.c_void_p()
+    st = lib.lbm_geometry_create(2, 5, None, 0, 0.0, 0.0, ctypes.byref(h))
+    assert st == lbm.LBM_EINVAL
+    assert b"nx >= 4" in lib.lbm_last_error()
+    bad = np.array([[5.0, 5.0, -1.0, 1, 0, -1]])
+    st = lib.lbm_geometry_create(10, 10, bad.ctypes.data_as(ctypes.c_void_p),
+                                 1, 0.1, 0.1, ctypes.byref(h))
+    assert st == lbm.LBM_EINVAL
+    g = lbm.Geometry(16, 8, np.zeros((0, 6)), 0.0, 0.0)
+    # solver calls on a geometry that was never uploaded
+    p = lbm.lbm_flow_params(0.8, 0.05, 10, 0.0, 10, lbm.LBM_F32)
+    info = lbm.lbm_solve_info()
+    st = lib.lbm_flow_solve(g.handle, ctypes.byref(p), ctypes.c_void_p(256),
+                            1 << 20, ctypes.c_void_p(512), None,
+                            ctypes.byref(info))
+    assert st == lbm.LBM_EINVAL and b"not uploaded" in lib.lbm_last_error()
+    prm = lbm.adr_params(3, 0.5, precision=lbm.LBM_F32)
+    assert lib.lbm_adr_ws_bytes(g.handle, ctypes.byref(prm)) == 0  # tau 1/2
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_efficiency([0.0, 0.0, 0.0], 3)
+    with pytest.raises(lbm.LBMError):
+        lbm.lbm_efficiency([1.0, 0.0, 0.0], 1)
+
+
+def test_efficiency_host_call(lib):
+    for flux in ([0.7, 0.2, 0.1], [3.0, 1.0, 0.0]):
+        assert lbm.lbm_efficiency(flux, 3) == pytest.approx(
+            oracle.efficiency(flux, 3), abs=1e-16)
+        assert lbm.lbm_efficiency(flux, 2) == pytest.approx(
+            oracle.efficiency(flux, 2), abs=1e-16)
+
+
+def test_workspace_sizes_scale_with_precision(lib):
+    g = lbm.Geometry(200, 100, inputs.single_fiber().fibers, 0.1, 0.0)
+    sizes = {}
+    for name, prec in lbm.PRECISIONS.items():
+        prm = lbm.adr_params(3, 0.62, precision=prec)
+        sizes[name] = lib.lbm_adr_ws_bytes(g.handle, ctypes.byref(prm))
+    plane = g.nx_pad * 100
+    # two population buffers dominate: 2 x 27 planes x element size
+    assert sizes["f64"] >= 2 * 27 * plane * 8
+    assert sizes["f32"] >= 2 * 27 * plane * 4
+    assert sizes["f16dev"] >= 2 * 27 * plane * 2
+    assert sizes["f16dev"] < sizes["f32"] < sizes["f64"]
+    assert lib.lbm_geometry_ws_bytes(g.handle) >= plane * (4 + 16)
