@@ -183,10 +183,31 @@ def _algorithmic_bytes(geom, w, precision):
     fl = links[links != 0xFFFFFFFF]
     ncat = 0
     for j in range(8):
-        ncat += int(((fl >> (4 * j)) & 0xF == 3).sum())
+        ncat += int((((fl >> (4 * j)) & 0xF) == 3).sum())
     per_fluid = SPECIES * 9 * 2 * es + 2 * ue + 4
     total = n_fluid * per_fluid + n_solid * 4 + ncat * 16
     return total, n_fluid, per_fluid
+
+
+# ---------------------------------------------------------------------------
+# multi-rank bookkeeping (replicas: no data-path collective)
+# ---------------------------------------------------------------------------
+def max_over_ranks(x: float, device=None) -> float:
+    """Slowest rank's value (the job is done when the last replica is)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or \
+            dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, elapsed_s: float,
+                   scale: float = 1e-6) -> float:
+    """Whole-job rate: units of every rank over the slowest rank's time."""
+    return units_per_rank * world / elapsed_s * scale
 
 
 # ---------------------------------------------------------------------------
@@ -334,13 +355,9 @@ def run_gpu(a):
     elapsed = t0.elapsed_time(t1) * 1e-3
     plain_s = sum(e0.elapsed_time(e1) for e0, e1 in ev_plain) * 1e-3
     launches_per_step = CHUNK + 2   # steps + partial-sum reduce + flux
-    if world > 1:
-        tt = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
-
+    elapsed = max_over_ranks(elapsed, dev)
     updates = SPECIES * w.nx * w.ny * CHUNK * a.steps
-    value = updates * world / elapsed / 1e6
+    value = job_throughput(updates, world, elapsed)
 
     # roofline of the dominant kernel (the fused ADR step)
     alg_bytes, n_fluid, per_fluid = _algorithmic_bytes(geom, w, a.precision)
@@ -368,11 +385,9 @@ def run_gpu(a):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = e0.elapsed_time(e1) * 1e-3
-    if world > 1:
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = SPECIES * w.nx * w.ny * CHUNK * e2e_steps * world / e2e_s / 1e6
+    e2e_s = max_over_ranks(e2e_s, dev)
+    e2e_value = job_throughput(SPECIES * w.nx * w.ny * CHUNK * e2e_steps,
+                               world, e2e_s)
 
     if rank == 0:
         line = {

@@ -277,7 +277,8 @@ class ADRProblem:
             self.steps(g, 1)
         c = self.conc(g)
         flux = self.flux(g, xp)
-        return dict(g=g, conc=c, flux=flux, eps=efficiency(flux, self.ns),
+        eps = efficiency(flux, self.ns) if self.ns >= 2 else None
+        return dict(g=g, conc=c, flux=flux, eps=eps,
                     residual=residual(c_prev, c))
 
     def solve(self, tol: float, check_every: int, max_steps: int, xp=None):

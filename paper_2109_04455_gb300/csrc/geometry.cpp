@@ -120,6 +120,7 @@ extern "C" lbm_status lbm_geometry_create(int32_t nx, int32_t ny,
           word |= t << (4 * (j - 1));
         }
         g->links[n] = word;
+        if (word != 0u) g->bnodes.push_back(n);
       }
     }
     g->n_solid = nsol;

@@ -2,7 +2,7 @@
 #include "lbm_launch_impl.cuh"
 
 namespace lbm {
-template cudaError_t launch_adr<PrecF32>(int, int, const AdrArgs &, dim3,
+template cudaError_t launch_adr<PrecF32>(int, int, const AdrArgs &,
                                             cudaStream_t);
 template cudaError_t launch_adr_flux<PrecF32>(int, const void *,
                                                  const uint32_t *, long long,

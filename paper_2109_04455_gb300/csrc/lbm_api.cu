@@ -14,16 +14,27 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
-cudaError_t launch_reduce(int k, const double *partials, long long nb,
-                          double *out, cudaStream_t st) {
+template <int K>
+static cudaError_t reduce_two_level(const double *partials, long long nb,
+                                   double *scratch, double *out,
+                                   cudaStream_t st) {
   const dim3 block(kReduceThreads);
+  const long long g = nb < kReduceGrid ? (nb > 0 ? nb : 1) : kReduceGrid;
+  const long long chunk = (nb + g - 1) / g;
+  reduce_partials_kernel<K><<<static_cast<unsigned>(g), block, 0, st>>>(
+      partials, nb, chunk, scratch);
+  reduce_partials_kernel<K><<<1, block, 0, st>>>(scratch, g, g, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(int k, const double *partials, long long nb,
+                          double *scratch, double *out, cudaStream_t st) {
   switch (k) {
-    case 2: reduce_partials_kernel<2><<<1, block, 0, st>>>(partials, nb, out); break;
-    case 4: reduce_partials_kernel<4><<<1, block, 0, st>>>(partials, nb, out); break;
-    case 6: reduce_partials_kernel<6><<<1, block, 0, st>>>(partials, nb, out); break;
+    case 2: return reduce_two_level<2>(partials, nb, scratch, out, st);
+    case 4: return reduce_two_level<4>(partials, nb, scratch, out, st);
+    case 6: return reduce_two_level<6>(partials, nb, scratch, out, st);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 namespace {
@@ -88,7 +99,7 @@ extern "C" const char *lbm_last_error(void) { return g_last_error.c_str(); }
 extern "C" size_t lbm_geometry_ws_bytes(const lbm_geometry *g) {
   if (!g) return 0;
   const size_t p = static_cast<size_t>(plane_of(g));
-  return align256(4 * p) + 2 * align256(8 * p);
+  return align256(4 * p) + 2 * align256(8 * p) + align256(8 * g->bnodes.size() + 8);
 }
 
 extern "C" lbm_status lbm_geometry_upload(lbm_geometry *g, void *dev_ws,
@@ -120,11 +131,17 @@ extern "C" lbm_status lbm_geometry_upload(lbm_geometry *g, void *dev_ws,
     e = cudaMemcpyAsync(d_kab, g->kab.data(), 8 * p, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_kbc, g->kbc.data(), 8 * p, cudaMemcpyHostToDevice, st);
+  long long *d_bnodes = reinterpret_cast<long long *>(
+      b + align256(4 * p) + 2 * align256(8 * p));
+  if (e == cudaSuccess && !g->bnodes.empty())
+    e = cudaMemcpyAsync(d_bnodes, g->bnodes.data(), 8 * g->bnodes.size(),
+                        cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail("lbm_geometry_upload", e);
   g->d_links = d_links;
   g->d_kab = d_kab;
   g->d_kbc = d_kbc;
+  g->d_bnodes = d_bnodes;
   g->uploaded = true;
   return LBM_OK;
 }
@@ -141,7 +158,8 @@ extern "C" size_t lbm_flow_ws_bytes(const lbm_geometry *g, int32_t precision) {
   const size_t p = static_cast<size_t>(plane_of(g));
   const size_t es = store_bytes(flow_prec(precision));
   return 2 * align256(9 * p * es) +
-         align256(static_cast<size_t>(grid_blocks(g)) * 2 * 8) + align256(64 * 8);
+         align256(static_cast<size_t>(grid_blocks(g)) * 2 * 8) +
+         align256(kReduceGrid * 2 * 8) + align256(64 * 8);
 }
 
 static cudaError_t flow_launch(int prec, int mode, const FlowArgs &a, dim3 grid,
@@ -183,8 +201,11 @@ extern "C" lbm_status lbm_flow_solve(const lbm_geometry *g,
   char *b = static_cast<char *>(f_ws);
   void *buf[2] = {b, b + bufb};
   double *partials = reinterpret_cast<double *>(b + 2 * bufb);
-  double *result = reinterpret_cast<double *>(
+  double *scratch = reinterpret_cast<double *>(
       b + 2 * bufb + align256(static_cast<size_t>(grid_blocks(g)) * 16));
+  double *result = reinterpret_cast<double *>(
+      b + 2 * bufb + align256(static_cast<size_t>(grid_blocks(g)) * 16) +
+      align256(kReduceGrid * 2 * 8));
   cudaStream_t st = as_stream(stream);
   const dim3 grid = lattice_grid(g);
 
@@ -225,7 +246,8 @@ extern "C" lbm_status lbm_flow_solve(const lbm_geometry *g,
     }
     cudaError_t e2 = step(kFlowU);
     if (e2 == cudaSuccess) e2 = step(kFlowCheck);
-    if (e2 == cudaSuccess) e2 = launch_reduce(2, partials, grid_blocks(g), result, st);
+    if (e2 == cudaSuccess)
+      e2 = launch_reduce(2, partials, grid_blocks(g), scratch, result, st);
     double h[2] = {0, 0};
     if (e2 == cudaSuccess)
       e2 = cudaMemcpyAsync(h, result, sizeof(h), cudaMemcpyDeviceToHost, st);
@@ -278,16 +300,16 @@ struct lbm_adr_solver {
   void *buf[2] = {nullptr, nullptr};
   void *cprev = nullptr;
   double *partials = nullptr;
+  double *scratch = nullptr;
   double *result = nullptr;
   int cur = 0;
   int64_t steps = 0;
   bool has_check = false;
-  dim3 grid;
   long long nb = 0;
 };
 
 struct AdrLayout {
-  size_t buf, cprev, partials, result, total;
+  size_t buf, cprev, partials, scratch, result, total;
 };
 
 static AdrLayout adr_layout(const lbm_geometry *g, const lbm_adr_params *p) {
@@ -296,9 +318,12 @@ static AdrLayout adr_layout(const lbm_geometry *g, const lbm_adr_params *p) {
   AdrLayout l{};
   l.buf = align256(ns * 9 * pl * store_bytes(p->precision));
   l.cprev = align256(ns * pl * compute_bytes(p->precision));
-  l.partials = align256(static_cast<size_t>(grid_blocks(g)) * 2 * ns * 8);
+  l.partials = align256(static_cast<size_t>(adr_partial_rows(
+                            g->nx_pad, g->ny, static_cast<long long>(g->bnodes.size()))) *
+                        2 * ns * 8);
+  l.scratch = align256(kReduceGrid * 2 * ns * 8);
   l.result = align256(64 * 8);
-  l.total = 2 * l.buf + l.cprev + l.partials + l.result;
+  l.total = 2 * l.buf + l.cprev + l.partials + l.scratch + l.result;
   return l;
 }
 
@@ -317,11 +342,11 @@ extern "C" size_t lbm_adr_ws_bytes(const lbm_geometry *g,
 }
 
 static cudaError_t adr_launch(int prec, int ns, int mode, const AdrArgs &a,
-                              dim3 grid, cudaStream_t st) {
+                              cudaStream_t st) {
   switch (prec) {
-    case LBM_F64: return launch_adr<PrecF64>(ns, mode, a, grid, st);
-    case LBM_F32: return launch_adr<PrecF32>(ns, mode, a, grid, st);
-    default: return launch_adr<PrecF16Dev>(ns, mode, a, grid, st);
+    case LBM_F64: return launch_adr<PrecF64>(ns, mode, a, st);
+    case LBM_F32: return launch_adr<PrecF32>(ns, mode, a, st);
+    default: return launch_adr<PrecF16Dev>(ns, mode, a, st);
   }
 }
 
@@ -393,9 +418,10 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
   s->buf[1] = b + l.buf;
   s->cprev = b + 2 * l.buf;
   s->partials = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev);
-  s->result = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials);
-  s->grid = lattice_grid(g);
-  s->nb = grid_blocks(g);
+  s->scratch = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials);
+  s->result = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials +
+                                         l.scratch);
+  s->nb = adr_partial_rows(g->nx_pad, g->ny, static_cast<long long>(g->bnodes.size()));
   AdrArgs &a = s->a;
   a.links = g->d_links;
   a.kab = g->d_kab;
@@ -403,6 +429,9 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
   a.u = u;
   a.cprev = s->cprev;
   a.partials = s->partials;
+  a.bnodes = g->d_bnodes;
+  a.nbnd = static_cast<long long>(g->bnodes.size());
+  a.part_off = 0;
   a.plane = plane_of(g);
   a.nx = g->nx;
   a.ny = g->ny;
@@ -433,7 +462,7 @@ extern "C" lbm_status lbm_adr_init(lbm_adr_solver *s, void *stream) {
   AdrArgs a = s->a;
   a.src = nullptr;
   a.dst = s->buf[0];
-  e = adr_launch(s->p.precision, s->p.nspecies, kAdrInit, a, s->grid, st);
+  e = adr_launch(s->p.precision, s->p.nspecies, kAdrInit, a, st);
   if (e != cudaSuccess) return cuda_fail("lbm_adr_init(kernel)", e);
   s->cur = 0;
   s->steps = 0;
@@ -447,7 +476,7 @@ static cudaError_t adr_step(lbm_adr_solver *s, int mode, cudaStream_t st) {
   a.dst = s->buf[s->cur ^ 1];
   s->cur ^= 1;
   ++s->steps;
-  return adr_launch(s->p.precision, s->p.nspecies, mode, a, s->grid, st);
+  return adr_launch(s->p.precision, s->p.nspecies, mode, a, st);
 }
 
 extern "C" lbm_status lbm_adr_run(lbm_adr_solver *s, int64_t nsteps,
@@ -467,7 +496,8 @@ extern "C" lbm_status lbm_adr_run(lbm_adr_solver *s, int64_t nsteps,
   if (!info) return LBM_OK;
   cudaError_t e = adr_step(s, kAdrCheck, st);
   if (e == cudaSuccess) e = adr_step(s, kAdrCheck, st);
-  if (e == cudaSuccess) e = launch_reduce(2 * ns, s->partials, s->nb, s->result, st);
+  if (e == cudaSuccess)
+    e = launch_reduce(2 * ns, s->partials, s->nb, s->scratch, s->result, st);
   if (e == cudaSuccess) e = adr_flux_launch(s, st);
   double h[16] = {0};
   if (e == cudaSuccess)

@@ -42,8 +42,10 @@ struct lbm_geometry {
   std::vector<uint8_t> solid;     // [ny][nx]
   std::vector<double> kab, kbc;   // [ny][nx_pad]
   std::vector<uint32_t> links;    // [ny][nx_pad]
+  std::vector<long long> bnodes;  // fluid nodes with a non-zero link word
   // device copies (borrowed from the caller's workspace after upload)
   const uint32_t *d_links = nullptr;
+  const long long *d_bnodes = nullptr;
   const double *d_kab = nullptr;
   const double *d_kbc = nullptr;
   bool uploaded = false;

@@ -24,7 +24,16 @@
 
 namespace lbm {
 
-constexpr int kBlockX = 128;      // threads per block (one row segment)
+// Launch shape of the lattice kernels (compile-time tuning knobs):
+//   LBM_BLOCK_X        threads per block = nodes of one row segment
+//   LBM_ADR_MIN_BLOCKS resident blocks per SM asked of the register allocator
+#ifndef LBM_BLOCK_X
+#define LBM_BLOCK_X 128
+#endif
+#ifndef LBM_ADR_MIN_BLOCKS
+#define LBM_ADR_MIN_BLOCKS 1
+#endif
+constexpr int kBlockX = LBM_BLOCK_X;
 constexpr int kReduceThreads = 256;
 
 // ---------------------------------------------------------------------------
@@ -74,21 +83,25 @@ __device__ __forceinline__ uint32_t nib(uint32_t word, int j) {
 }
 
 // ---------------------------------------------------------------------------
-// deterministic block reduction of K doubles (fixed order for a fixed block
-// size); result valid in thread 0
+// deterministic block reduction of K values: warp shuffles in the value type
+// A (float on the float paths, where double shuffles would cost more than the
+// lattice update on this part's narrow FP64 pipe), then the warp sums added
+// in double in a fixed order.  Result valid in thread 0.
 // ---------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K]) {
+template <int K, typename A>
+__device__ __forceinline__ void block_sum(const A (&v)[K], double (&out)[K]) {
   __shared__ double red[32][K];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  A w[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
+    w[k] = v[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    for (int o = 16; o > 0; o >>= 1) w[k] += __shfl_down_sync(0xffffffffu, w[k], o);
   }
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) red[warp][k] = v[k];
+    for (int k = 0; k < K; ++k) red[warp][k] = double(w[k]);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -96,11 +109,22 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += red[w][k];
-      v[k] = s;
+      for (int i = 0; i < nw; ++i) s += red[i][k];
+      out[k] = s;
     }
   }
 }
+
+// two-wide vector of a storage / compute type
+template <typename S> struct Vec2;
+template <> struct Vec2<double> { using type = double2; };
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<__half> { using type = __half2; };
+
+template <typename S>
+__device__ __forceinline__ S zero_of() { return S(0); }
+template <>
+__device__ __forceinline__ __half zero_of<__half>() { return __float2half_rn(0.0f); }
 
 // ---------------------------------------------------------------------------
 // ADR
@@ -112,7 +136,10 @@ struct AdrArgs {
   const double *kab, *kbc;  // [plane]
   const void *u;            // T [2][plane]
   void *cprev;              // T [ns][plane]     (check steps)
-  double *partials;         // [nblocks][2*ns]   (check steps)
+  double *partials;         // [rows][2*ns]      (check steps)
+  const long long *bnodes;  // boundary fluid nodes (link word != 0)
+  long long nbnd;           // number of boundary nodes
+  long long part_off;       // first partial row of the boundary kernel
   long long plane;          // ny * nx_pad
   int nx, ny, nx_pad;
   int abb_all;              // anti-bounce-back inlet for every species
@@ -123,145 +150,299 @@ struct AdrArgs {
 
 enum AdrMode { kAdrStep = 0, kAdrCheck = 1, kAdrInit = 2 };
 
-template <class P, int NS, int MODE>
-__global__ void __launch_bounds__(kBlockX) adr_kernel(const AdrArgs a) {
+// value added back to a stored population (deviation storage only)
+template <class P>
+__device__ __forceinline__ typename P::T adr_shift(const AdrArgs &a, int s, int i) {
+  using T = typename P::T;
+  return P::kDev ? Lattice<T>::w(i) * T(a.cref[s]) : T(0);
+}
+
+template <class P>
+__device__ __forceinline__ typename P::T adr_ld(const AdrArgs &a, int s, int i,
+                                                long long m) {
+  const typename P::S *src = static_cast<const typename P::S *>(a.src);
+  return P::load(src[(long long)(s * 9 + i) * a.plane + m]) + adr_shift<P>(a, s, i);
+}
+
+// equilibrium factors E_i(u), shared by every species:
+// g_i^eq = C * E_i, E_i = w_i (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
+template <typename T>
+__device__ __forceinline__ void eq_factors(T ux, T uy, T (&E)[9]) {
+  const T uu = ux * ux + uy * uy;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const T cu = T(cx(i)) * ux + T(cy(i)) * uy;
+    E[i] = Lattice<T>::w(i) * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+  }
+}
+
+// The species are updated one after the other (A, then B, then C): the
+// sources are triangular (A's depends on C_A, B's on C_A and C_B, C's on
+// C_B), so every source term is known when its species is collided, and only
+// one species' nine populations need to be live at a time.
+
+// Boundary node x (link word lw != 0), species s: replace every population
+// whose pull source is not a fluid node by the rule of that source's link
+// type (Eq. BC and bounce-back), reading the node's own post-collision values.
+template <class P>
+__device__ __forceinline__ void adr_boundary(const AdrArgs &a, int s,
+                                             uint32_t lw, long long n, int x,
+                                             typename P::T (&g)[9]) {
+  using T = typename P::T;
+  T cb = T(0);
+  if (x == a.nx - 1) {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) cb += adr_ld<P>(a, s, j, n);
+  }
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const uint32_t t = nib(lw, opp(i));
+    if (t == kFluid) continue;
+    const T back = adr_ld<P>(a, s, opp(i), n);
+    if (t == kInlet) {
+      g[i] = (s == 0 || a.abb_all) ? -back + T(2) * Lattice<T>::w(i) * T(a.cin[s])
+                                   : back;
+    } else if (t == kOutlet) {
+      g[i] = -back + T(2) * Lattice<T>::w(i) * cb;
+    } else {  // wall, inert or catalytic fiber: bounce-back
+      g[i] = back;
+    }
+  }
+}
+
+// BGK collision of species s towards C E_i, then its Dawson source on links
+// into catalytic fiber nodes (Eq. source_lbm):
+//   Q_A = -k_AB w C_A,  Q_B = +k_AB w C_A - k_BC w C_B,  Q_C = +k_BC w C_B.
+// C[] holds the pre-collision concentrations of species 0..s; returns C_s.
+template <class P, int NS>
+__device__ __forceinline__ typename P::T adr_collide(const AdrArgs &a, int s,
+                                                     uint32_t lw, long long n,
+                                                     const typename P::T (&E)[9],
+                                                     typename P::T (&g)[9],
+                                                     typename P::T (&C)[NS]) {
+  using T = typename P::T;
+  T c = T(0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) c += g[i];
+  C[s] = c;
+  const T om = T(a.omega[s]);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) g[i] = g[i] + om * (c * E[i] - g[i]);
+  if (lw != 0u) {
+    const long long np = a.nx_pad;
+#pragma unroll
+    for (int j = 1; j < 9; ++j) {
+      if (nib(lw, j) != kCat) continue;
+      const long long m = n + cy(j) * np + cx(j);
+      const T wj = Lattice<T>::w(j);
+      if (s == 0) {
+        g[j] -= T(a.kab[m]) * wj * C[0];
+      } else if (s == 1) {
+        const T ra = T(a.kab[m]) * wj * C[0];
+        const T rb = (NS >= 3) ? T(a.kbc[m]) * wj * C[NS >= 2 ? 1 : 0] : T(0);
+        g[j] += ra - rb;
+      } else {
+        g[j] += T(a.kbc[m]) * wj * C[NS >= 2 ? 1 : 0];
+      }
+    }
+  }
+  return c;
+}
+
+// One node per thread, every link rule handled in place.  LIST = false: the
+// whole lattice (initial state; also the plain one-kernel step).  LIST = true:
+// only the boundary nodes of a.bnodes, after the bulk kernel (below) has
+// written the interior formula everywhere; its partial sums go to rows
+// a.part_off + block.
+template <class P, int NS, int MODE, bool LIST>
+__global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
+    adr_node_kernel(const AdrArgs a) {
   using S = typename P::S;
   using T = typename P::T;
-  const int x = blockIdx.x * kBlockX + threadIdx.x;
-  const int y = blockIdx.y;
-  const long long n = (long long)y * a.nx_pad + x;
+  long long n;
+  int x;
+  uint32_t lw;
+  if (LIST) {
+    const long long t = (long long)blockIdx.x * kBlockX + threadIdx.x;
+    n = t < a.nbnd ? a.bnodes[t] : 0;
+    x = static_cast<int>(n % a.nx_pad);
+    lw = t < a.nbnd ? a.links[n] : kSolidNode;
+  } else {
+    x = blockIdx.x * kBlockX + threadIdx.x;
+    n = (long long)blockIdx.y * a.nx_pad + x;
+    lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
+  }
   const long long plane = a.plane;
-  const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
-  double acc[2 * NS];
+  T acc[2 * NS];
 #pragma unroll
-  for (int k = 0; k < 2 * NS; ++k) acc[k] = 0.0;
+  for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
 
   if (lw != kSolidNode) {
-    const S *__restrict__ src = static_cast<const S *>(a.src);
     S *__restrict__ dst = static_cast<S *>(a.dst);
     const T *__restrict__ U = static_cast<const T *>(a.u);
-    const T ux = U[n], uy = U[plane + n];
     const long long np = (long long)a.nx_pad;
-
-    // shift of the stored deviation
-    auto shift = [&](int s, int i) -> T {
-      return P::kDev ? Lattice<T>::w(i) * T(a.cref[s]) : T(0);
-    };
-    auto ld = [&](int s, int i, long long m) -> T {
-      return P::load(src[(long long)(s * 9 + i) * plane + m]) + shift(s, i);
-    };
-
-    // equilibrium factors E_i(u), shared by every species:
-    // g_i^eq = C * E_i, E_i = w_i (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
     T E[9];
-    {
-      const T uu = ux * ux + uy * uy;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const T cu = T(cx(i)) * ux + T(cy(i)) * uy;
-        E[i] = Lattice<T>::w(i) *
-               (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
-      }
-    }
-
-    T g[NS][9];
-    if (MODE == kAdrInit) {
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        const T c0 = (s == 0) ? T(1) : T(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) g[s][i] = c0 * E[i];
-      }
-    } else if (lw == 0u) {
-      // interior node: every population streams from a fluid neighbour
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) g[s][i] = ld(s, i, n - (cy(i) * np + cx(i)));
-      }
-    } else {
-      // boundary node: pull or apply the rule of the source's link type
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        T cb = T(0);
-        if (x == a.nx - 1) {
-#pragma unroll
-          for (int j = 0; j < 9; ++j) cb += ld(s, j, n);
-        }
-        g[s][0] = ld(s, 0, n);
-#pragma unroll
-        for (int i = 1; i < 9; ++i) {
-          const uint32_t t = nib(lw, opp(i));
-          if (t == kFluid) {
-            g[s][i] = ld(s, i, n - (cy(i) * np + cx(i)));
-          } else if (t == kInlet) {
-            const T back = ld(s, opp(i), n);
-            g[s][i] = (s == 0 || a.abb_all)
-                          ? -back + T(2) * Lattice<T>::w(i) * T(a.cin[s])
-                          : back;
-          } else if (t == kOutlet) {
-            g[s][i] = -ld(s, opp(i), n) + T(2) * Lattice<T>::w(i) * cb;
-          } else {  // wall, inert or catalytic fiber: bounce-back
-            g[s][i] = ld(s, opp(i), n);
-          }
-        }
-      }
-    }
-
-    // concentrations and BGK collision
+    eq_factors<T>(U[n], U[plane + n], E);
     T C[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      T c = T(0);
+      T g[9];
+      if (MODE == kAdrInit) {
+        const T c0 = (s == 0) ? T(1) : T(0);
 #pragma unroll
-      for (int i = 0; i < 9; ++i) c += g[s][i];
-      C[s] = c;
-      const T om = T(a.omega[s]);
+        for (int i = 0; i < 9; ++i) g[i] = c0 * E[i];
+      } else {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) g[s][i] = g[s][i] + om * (c * E[i] - g[s][i]);
-    }
-
-    // Dawson source on links into catalytic fiber nodes
-    if (lw != 0u) {
-#pragma unroll
-      for (int j = 1; j < 9; ++j) {
-        if (nib(lw, j) == kCat) {
-          const long long m = n + cy(j) * np + cx(j);
-          const T wj = Lattice<T>::w(j);
-          const T ra = T(a.kab[m]) * wj * C[0];
-          const T rb = (NS >= 3) ? T(a.kbc[m]) * wj * C[NS >= 2 ? 1 : 0] : T(0);
-          g[0][j] -= ra;
-          if (NS >= 2) g[NS >= 2 ? 1 : 0][j] += ra - rb;
-          if (NS >= 3) g[NS >= 3 ? 2 : 0][j] += rb;
+        for (int i = 0; i < 9; ++i) {
+          // pull from x - c_i when that node is fluid (always for lw == 0)
+          if (i == 0 || lw == 0u || nib(lw, opp(i)) == kFluid)
+            g[i] = adr_ld<P>(a, s, i, n - (cy(i) * np + cx(i)));
         }
+        if (lw != 0u) adr_boundary<P>(a, s, lw, n, x, g);
       }
-    }
-
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
+      const T c = adr_collide<P, NS>(a, s, lw, n, E, g, C);
 #pragma unroll
       for (int i = 0; i < 9; ++i)
-        dst[(long long)(s * 9 + i) * plane + n] = P::store(g[s][i] - shift(s, i));
-    }
-
-    if (MODE == kAdrCheck) {
-      T *cp = static_cast<T *>(a.cprev);
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        const T prev = cp[s * plane + n];
-        acc[2 * s] = fabs(double(C[s]) - double(prev));
-        acc[2 * s + 1] = fabs(double(C[s]));
-        cp[s * plane + n] = C[s];
+        dst[(long long)(s * 9 + i) * plane + n] = P::store(g[i] - adr_shift<P>(a, s, i));
+      if (MODE == kAdrCheck) {
+        T *cp = static_cast<T *>(a.cprev);
+        acc[2 * s] = fabs(c - cp[s * plane + n]);
+        acc[2 * s + 1] = fabs(c);
+        cp[s * plane + n] = c;
       }
     }
   }
 
   if (MODE == kAdrCheck) {
-    block_sum<2 * NS>(acc);
+    double tot[2 * NS];
+    block_sum<2 * NS, T>(acc, tot);
+    if (threadIdx.x == 0) {
+      const long long b = LIST ? a.part_off + blockIdx.x
+                               : (long long)blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+      for (int k = 0; k < 2 * NS; ++k) a.partials[b * (2 * NS) + k] = tot[k];
+    }
+  }
+}
+
+// Bulk step, two nodes per thread (x0 = 2 t, x0 + 1): the interior formula
+// (pull from x - c_i, BGK, no source) for every fluid node, without looking
+// at link types, so the kernel has no per-direction branches.  Boundary
+// nodes get a provisional value here that adr_node_kernel<..., LIST = true>
+// overwrites right after; their residual terms and C are left to that kernel.
+// Each population plane is read with aligned two-wide vector loads; the
+// neighbour element a horizontal or diagonal pull needs (x0 - 1 or x0 + 2)
+// comes from the adjacent lane by a warp shuffle, and only the first / last
+// lane of a warp issues one extra scalar load for it.  Reads outside the
+// lattice rows or row ends are skipped (zeros), so every access stays in
+// bounds.  Stores are two-wide and aligned.
+template <class P, int NS, int MODE>
+__global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
+    adr_bulk_kernel(const AdrArgs a) {
+  using S = typename P::S;
+  using T = typename P::T;
+  using VS = typename Vec2<S>::type;
+  using VT = typename Vec2<T>::type;
+  const int lane = threadIdx.x & 31;
+  const int x0 = 2 * (blockIdx.x * kBlockX + threadIdx.x);
+  const int y = blockIdx.y;
+  const long long np = a.nx_pad, plane = a.plane;
+  const bool valid = x0 < a.nx_pad;  // nx_pad is even: x0 + 1 is inside too
+  const long long n0 = (long long)y * np + x0;
+  const S *__restrict__ src = static_cast<const S *>(a.src);
+  S *__restrict__ dst = static_cast<S *>(a.dst);
+
+  uint2 lw = make_uint2(kSolidNode, kSolidNode);
+  VT ux = {T(0), T(0)}, uy = {T(0), T(0)};
+  if (valid) {
+    lw = *reinterpret_cast<const uint2 *>(a.links + n0);
+    const T *U = static_cast<const T *>(a.u);
+    ux = *reinterpret_cast<const VT *>(U + n0);
+    uy = *reinterpret_cast<const VT *>(U + plane + n0);
+  }
+  const bool fluid0 = lw.x != kSolidNode, fluid1 = lw.y != kSolidNode;
+  const bool inner0 = lw.x == 0u, inner1 = lw.y == 0u;
+  T E0[9], E1[9];
+  eq_factors<T>(ux.x, uy.x, E0);
+  eq_factors<T>(ux.y, uy.y, E1);
+
+  T acc[2 * NS];
+#pragma unroll
+  for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
+
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    T g0[9], g1[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int row = y - cy(i);
+      const bool rowok = valid && row >= 0 && row < a.ny;
+      const long long base = (long long)(s * 9 + i) * plane + (long long)row * np + x0;
+      S e0 = zero_of<S>(), e1 = zero_of<S>();
+      if (rowok) {
+        const VS v = *reinterpret_cast<const VS *>(src + base);
+        e0 = v.x;
+        e1 = v.y;
+      }
+      S lo, hi;
+      if (cx(i) == 0) {
+        lo = e0;
+        hi = e1;
+      } else if (cx(i) > 0) {  // sources x0 - 1, x0
+        S left = __shfl_up_sync(0xffffffffu, e1, 1);
+        if (lane == 0) left = (rowok && x0 >= 1) ? src[base - 1] : zero_of<S>();
+        lo = left;
+        hi = e0;
+      } else {  // sources x0 + 1, x0 + 2
+        S right = __shfl_down_sync(0xffffffffu, e0, 1);
+        if (lane == 31) right = (rowok && x0 + 2 < a.nx_pad) ? src[base + 2] : zero_of<S>();
+        lo = e1;
+        hi = right;
+      }
+      const T sh = adr_shift<P>(a, s, i);
+      g0[i] = P::load(lo) + sh;
+      g1[i] = P::load(hi) + sh;
+    }
+
+    T c0 = T(0), c1 = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      c0 += g0[i];
+      c1 += g1[i];
+    }
+    const T om = T(a.omega[s]);
+    if (valid) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const T sh = adr_shift<P>(a, s, i);
+        VS v;   // solid / padding nodes store zeros (never read)
+        v.x = fluid0 ? P::store(g0[i] + om * (c0 * E0[i] - g0[i]) - sh) : zero_of<S>();
+        v.y = fluid1 ? P::store(g1[i] + om * (c1 * E1[i] - g1[i]) - sh) : zero_of<S>();
+        *reinterpret_cast<VS *>(dst + (long long)(s * 9 + i) * plane + n0) = v;
+      }
+      if (MODE == kAdrCheck) {
+        T *cp = static_cast<T *>(a.cprev) + s * plane + n0;
+        if (inner0) {
+          acc[2 * s] += fabs(c0 - cp[0]);
+          acc[2 * s + 1] += fabs(c0);
+          cp[0] = c0;
+        }
+        if (inner1) {
+          acc[2 * s] += fabs(c1 - cp[1]);
+          acc[2 * s + 1] += fabs(c1);
+          cp[1] = c1;
+        }
+      }
+    }
+  }
+
+  if (MODE == kAdrCheck) {
+    double tot[2 * NS];
+    block_sum<2 * NS, T>(acc, tot);
     if (threadIdx.x == 0) {
       const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
 #pragma unroll
-      for (int k = 0; k < 2 * NS; ++k) a.partials[b * (2 * NS) + k] = acc[k];
+      for (int k = 0; k < 2 * NS; ++k) a.partials[b * (2 * NS) + k] = tot[k];
     }
   }
 }
@@ -295,28 +476,36 @@ __global__ void __launch_bounds__(kReduceThreads)
       acc[s] += v;
     }
   }
-  block_sum<NS>(acc);
+  double tot[NS];
+  block_sum<NS, double>(acc, tot);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) out[s] = acc[s] / double(ny);
+    for (int s = 0; s < NS; ++s) out[s] = tot[s] / double(ny);
   }
 }
 
-// Sum nb rows of K partials in a fixed order into out[0..K).  One block.
+// Sum rows of K partials in a fixed order.  Block b of the grid adds the
+// rows [b*chunk, (b+1)*chunk) into out[b*K + k]; a second launch with one
+// block folds those.  Deterministic for a fixed grid.
 template <int K>
 __global__ void __launch_bounds__(kReduceThreads)
-    reduce_partials_kernel(const double *partials, long long nb, double *out) {
+    reduce_partials_kernel(const double *partials, long long nb, long long chunk,
+                           double *out) {
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) acc[k] = 0.0;
-  for (long long b = threadIdx.x; b < nb; b += blockDim.x) {
+  const long long lo = (long long)blockIdx.x * chunk;
+  long long hi = lo + chunk;
+  if (hi > nb) hi = nb;
+  for (long long b = lo + threadIdx.x; b < hi; b += blockDim.x) {
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] += partials[b * K + k];
   }
-  block_sum<K>(acc);
+  double tot[K];
+  block_sum<K, double>(acc, tot);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = acc[k];
+    for (int k = 0; k < K; ++k) out[(long long)blockIdx.x * K + k] = tot[k];
   }
 }
 
@@ -346,7 +535,7 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
   const long long n = (long long)y * a.nx_pad + x;
   const long long plane = a.plane;
   const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
-  double acc[2] = {0.0, 0.0};
+  T acc[2] = {T(0), T(0)};
   T *U = static_cast<T *>(a.u);
 
   if (lw != kSolidNode) {
@@ -428,8 +617,8 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
     }
     if (MODE == kFlowU || MODE == kFlowCheck) {
       if (MODE == kFlowCheck) {
-        acc[0] = fabs(double(ux) - double(U[n])) + fabs(double(uy) - double(U[plane + n]));
-        acc[1] = fabs(double(ux)) + fabs(double(uy));
+        acc[0] = fabs(ux - U[n]) + fabs(uy - U[plane + n]);
+        acc[1] = fabs(ux) + fabs(uy);
       }
       U[n] = ux;
       U[plane + n] = uy;
@@ -440,11 +629,12 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
   }
 
   if (MODE == kFlowCheck) {
-    block_sum<2>(acc);
+    double tot[2];
+    block_sum<2, T>(acc, tot);
     if (threadIdx.x == 0) {
       const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-      a.partials[b * 2] = acc[0];
-      a.partials[b * 2 + 1] = acc[1];
+      a.partials[b * 2] = tot[0];
+      a.partials[b * 2 + 1] = tot[1];
     }
   }
 }
@@ -452,9 +642,35 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
 // ---------------------------------------------------------------------------
 // launchers (one translation unit per precision instantiates them)
 // ---------------------------------------------------------------------------
+// A time step is the bulk kernel (two nodes per thread, interior formula)
+// followed by the boundary kernel over the boundary-node list; with
+// LBM_ADR_SPLIT=0 it is the one-node kernel over the whole lattice instead.
+#ifndef LBM_ADR_SPLIT
+#define LBM_ADR_SPLIT 1
+#endif
+inline dim3 adr_bulk_grid(int nx_pad, int ny) {
+  return dim3(static_cast<unsigned>((nx_pad + 2 * kBlockX - 1) / (2 * kBlockX)),
+              static_cast<unsigned>(ny));
+}
+inline dim3 adr_node_grid(int nx_pad, int ny) {
+  return dim3(static_cast<unsigned>((nx_pad + kBlockX - 1) / kBlockX),
+              static_cast<unsigned>(ny));
+}
+inline long long adr_list_blocks(long long nbnd) {
+  return (nbnd + kBlockX - 1) / kBlockX;
+}
+// partial-sum rows written by one check step
+inline long long adr_partial_rows(int nx_pad, int ny, long long nbnd) {
+  if (!LBM_ADR_SPLIT) {
+    const dim3 g = adr_node_grid(nx_pad, ny);
+    return static_cast<long long>(g.x) * g.y;
+  }
+  const dim3 g = adr_bulk_grid(nx_pad, ny);
+  return static_cast<long long>(g.x) * g.y + adr_list_blocks(nbnd);
+}
+
 template <class P>
-cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, dim3 grid,
-                       cudaStream_t st);
+cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, cudaStream_t st);
 template <class P>
 cudaError_t launch_adr_flux(int ns, const void *g, const uint32_t *links,
                             long long plane, int nx_pad, int ny, int xp,
@@ -462,7 +678,10 @@ cudaError_t launch_adr_flux(int ns, const void *g, const uint32_t *links,
 template <class P>
 cudaError_t launch_flow(int mode, const FlowArgs &a, dim3 grid, cudaStream_t st);
 
+// Two-level deterministic sum of nb rows of k partials into out[0..k);
+// scratch holds kReduceGrid * k doubles.
+constexpr int kReduceGrid = 256;
 cudaError_t launch_reduce(int k, const double *partials, long long nb,
-                          double *out, cudaStream_t st);
+                          double *scratch, double *out, cudaStream_t st);
 
 }  // namespace lbm

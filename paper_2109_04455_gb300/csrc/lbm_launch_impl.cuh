@@ -7,26 +7,45 @@
 
 namespace lbm {
 
-template <class P>
-cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, dim3 grid,
-                       cudaStream_t st) {
+template <class P, int NS>
+static cudaError_t launch_adr_ns(int mode, const AdrArgs &a, cudaStream_t st) {
   const dim3 block(kBlockX);
-#define LBM_ADR_CASE(NS, MODE)                              \
-  if (ns == NS && mode == MODE) {                           \
-    adr_kernel<P, NS, MODE><<<grid, block, 0, st>>>(a);     \
-    return cudaGetLastError();                              \
+  if (mode == kAdrInit) {
+    adr_node_kernel<P, NS, kAdrInit, false>
+        <<<adr_node_grid(a.nx_pad, a.ny), block, 0, st>>>(a);
+    return cudaGetLastError();
   }
-  LBM_ADR_CASE(1, kAdrStep)
-  LBM_ADR_CASE(1, kAdrCheck)
-  LBM_ADR_CASE(1, kAdrInit)
-  LBM_ADR_CASE(2, kAdrStep)
-  LBM_ADR_CASE(2, kAdrCheck)
-  LBM_ADR_CASE(2, kAdrInit)
-  LBM_ADR_CASE(3, kAdrStep)
-  LBM_ADR_CASE(3, kAdrCheck)
-  LBM_ADR_CASE(3, kAdrInit)
-#undef LBM_ADR_CASE
-  return cudaErrorInvalidValue;
+  if (!LBM_ADR_SPLIT) {
+    if (mode == kAdrStep)
+      adr_node_kernel<P, NS, kAdrStep, false>
+          <<<adr_node_grid(a.nx_pad, a.ny), block, 0, st>>>(a);
+    else
+      adr_node_kernel<P, NS, kAdrCheck, false>
+          <<<adr_node_grid(a.nx_pad, a.ny), block, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  const dim3 bg = adr_bulk_grid(a.nx_pad, a.ny);
+  AdrArgs b = a;
+  b.part_off = static_cast<long long>(bg.x) * bg.y;
+  const unsigned lb = static_cast<unsigned>(adr_list_blocks(a.nbnd));
+  if (mode == kAdrStep) {
+    adr_bulk_kernel<P, NS, kAdrStep><<<bg, block, 0, st>>>(a);
+    if (lb) adr_node_kernel<P, NS, kAdrStep, true><<<lb, block, 0, st>>>(b);
+  } else {
+    adr_bulk_kernel<P, NS, kAdrCheck><<<bg, block, 0, st>>>(a);
+    if (lb) adr_node_kernel<P, NS, kAdrCheck, true><<<lb, block, 0, st>>>(b);
+  }
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, cudaStream_t st) {
+  switch (ns) {
+    case 1: return launch_adr_ns<P, 1>(mode, a, st);
+    case 2: return launch_adr_ns<P, 2>(mode, a, st);
+    case 3: return launch_adr_ns<P, 3>(mode, a, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <class P>

@@ -88,7 +88,9 @@ def test_flow_f64_matches_oracle(name):
     assert np.all(ug[:, :, nx:] == 0.0)
     assert np.all(ug[:, :, :nx][:, solid == 1] == 0.0)
     assert info["steps"] == steps
-    assert info["residual"] == pytest.approx(res, rel=1e-6, abs=1e-16)
+    # the residual is a difference of nearly equal fields: compare to the
+    # rounding level of the velocities once the flow has settled
+    assert info["residual"] == pytest.approx(res, rel=1e-6, abs=1e-14)
 
 
 def test_flow_f32_matches_oracle():
@@ -183,17 +185,21 @@ def test_adr_flux_plane_anywhere():
                                                 (lbm.LBM_F16DEV, 1e-3, 1e-2)])
 def test_adr_reduced_precision(prec, tol_eps, tol_c):
     nx, ny, fib, k1, k2, solid, kab, kbc, ux, uy = _oracle_case("ragged")
-    steps = 600
+    steps, xp = 1500, 130
     geom = lbm.Geometry(nx, ny, fib, k1, k2).upload()
     u = _dev_u(ux, uy, geom.nx_pad, torch.float32)
     conc, info = _run_gpu_adr(geom, u, 3, [0.62] * 3, [1, 0, 0], prec, steps,
-                              xp=150)
+                              xp=xp)
     prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, [0.62] * 3, [1, 0, 0])
-    ref = prob.run(steps, xp=150)
+    ref = prob.run(steps, xp=xp)
     rel = np.linalg.norm(conc - ref["conc"]) / np.linalg.norm(ref["conc"])
     assert rel < tol_c
-    assert ref["eps"] > 1e-3     # plane downstream of the catalysts
     assert abs(info["eps"] - ref["eps"]) < tol_eps
+    # the A->B efficiency on this plane is O(0.1), so the tolerance bites
+    e2_gpu = lbm.lbm_efficiency(list(info["flux"][:2]) + [0.0], 2)
+    e2_ref = oracle.efficiency(ref["flux"][:2], 2)
+    assert e2_ref > 10 * tol_eps
+    assert abs(e2_gpu - e2_ref) < tol_eps
 
 
 def test_adr_steady_solve_f64():
