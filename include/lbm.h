@@ -198,6 +198,36 @@ lbm_status lbm_adr_solve(const lbm_geometry *g, const lbm_adr_params *p,
                          const void *u, void *ws, size_t ws_bytes,
                          void *conc_out, void *stream, lbm_solve_info *info);
 
+/* ------------------------------------------------------------------------ */
+/* Discrete adjoint of the ADR lattice: gradient of the efficiency (Eq. A-B) */
+/* with respect to the per-node rates k_AB, k_BC of the fiber nodes, and to  */
+/* relaxed per-fiber catalyst weights w_f (k_AB = w_f k1, k_BC = (1-w_f) k2) */
+/* through the chain rule.  The frozen-flow ADR step is affine in the state, */
+/* g*(t+1) = K (P g*(t) + b) (P: pull and link rules, K: per-node collision  */
+/* and the Dawson source of Eq. source_lbm), so the adjoint of the           */
+/* pre-collision populations solves nu = K^T (P^T nu + l), l = d eps/d g* on */
+/* the flux plane; it is iterated from nu = 0 with the transposed (gather)    */
+/* stream-collide.  Then d eps/dk(n) = sum over the links x -> n of          */
+/* mu^T dK/dk g, mu = P^T nu + l.  Not in the paper: it differentiates the   */
+/* paper's discrete scheme.                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Device bytes of the adjoint workspace (LBM_F64 or LBM_F32 precision). */
+size_t lbm_adr_adjoint_ws_bytes(const lbm_geometry *g, const lbm_adr_params *p);
+
+/* Adjoint at the solver's current state, which must come from a run with
+ * info (lbm_adr_run / lbm_adr_solve loop) so that its concentrations are
+ * recorded; precision LBM_F64 or LBM_F32 (populations and adjoint alike).
+ * Iterates max_steps times (tol <= 0) or in chunks of check_every until the
+ * relative L1 change of nu per iteration is below tol.  Outputs (device,
+ * zeroed first, accumulated in double): dkab, dkbc [ny][nx_pad] (non-zero on
+ * fiber nodes only), dw [nfibers] (may be NULL).  info: iterations, adjoint
+ * residual, converged, and the forward outfluxes and efficiency used. */
+lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps, double tol,
+                           int32_t check_every, void *ws, size_t ws_bytes,
+                           void *dkab, void *dkbc, void *dw, void *stream,
+                           lbm_solve_info *info);
+
 /* Eq. (A-B): eps = N_B/(N_A+N_B) for nspecies 2, N_C/(N_A+N_B+N_C) for 3.
  * Host arithmetic only.  LBM_EINVAL for other nspecies or a zero sum. */
 lbm_status lbm_efficiency(const double *flux, int32_t nspecies, double *eps);

@@ -100,6 +100,12 @@ def _load():
             lib.orc_adr_steps.restype = I
             lib.orc_adr_flux.argtypes = [I, I, I, P, P, P, P, P, P, I, P, I,
                                          P]
+            lib.orc_adr_adjoint_steps.argtypes = [I, I, I, P, P, P, P, P, P, I,
+                                                  P, I, L, P, P]
+            lib.orc_adr_adjoint_steps.restype = I
+            lib.orc_adr_gradient.argtypes = [I, I, I, P, P, P, P, P, P, I, P,
+                                             I, P, P, P, P]
+            lib.orc_fiber_ids.argtypes = [I, I, I, P, P]
             _lib = lib
     return _lib
 
@@ -294,6 +300,75 @@ class ADRProblem:
                 out["steps"] = done
                 out["converged"] = out["residual"] < tol
                 return out
+
+
+def efficiency_sensitivity(flux, ns: int) -> np.ndarray:
+    """d eps / d N_s of Eq. (A-B) (zeros for absent species)."""
+    f = [float(v) for v in flux]
+    d = np.zeros(3)
+    if ns == 2:
+        tot = f[0] + f[1]
+        d[0] = -f[1] / tot**2
+        d[1] = f[0] / tot**2
+    elif ns == 3:
+        tot = f[0] + f[1] + f[2]
+        d[0] = d[1] = -f[2] / tot**2
+        d[2] = (f[0] + f[1]) / tot**2
+    else:
+        raise ValueError("efficiency needs 2 or 3 species")
+    return d
+
+
+def fiber_ids(nx: int, ny: int, fibers) -> np.ndarray:
+    """Owning fiber of each node (first in list order), -1 on fluid."""
+    lib = _load()
+    fib = _f64(np.asarray(fibers, dtype=np.float64).reshape(-1, 6))
+    ids = np.zeros((ny, nx), dtype=np.int32)
+    lib.orc_fiber_ids(nx, ny, fib.shape[0], _p(fib), _p(ids))
+    return ids
+
+
+def adjoint(prob: "ADRProblem", g_steady: np.ndarray, nsteps: int,
+            xp: int | None = None, nu: np.ndarray | None = None):
+    """Discrete adjoint of the ADR lattice at the state ``g_steady``
+    (pre-collision): ``nsteps`` iterations nu <- K^T (P^T nu + l) from
+    ``nu`` (zero by default), then the rate gradients.  Returns
+    dict(nu, dkab, dkbc, dNds, eps)."""
+    lib = _load()
+    ny, nx = prob.solid.shape
+    if xp is None:
+        xp = nx - 3
+    flux = prob.flux(g_steady, xp)
+    dnds = _f64(efficiency_sensitivity(flux, prob.ns))
+    if nu is None:
+        nu = np.zeros_like(g_steady)
+    tmp = np.empty_like(nu)
+    rc = lib.orc_adr_adjoint_steps(nx, ny, prob.ns, _p(prob.solid),
+                                   _p(prob.kab), _p(prob.kbc), _p(prob.ux),
+                                   _p(prob.uy), _p(prob.tau), prob.flags,
+                                   _p(dnds), int(xp), int(nsteps), _p(nu),
+                                   _p(tmp))
+    if rc:
+        raise ValueError("orc_adr_adjoint_steps: bad arguments")
+    dkab = np.zeros((ny, nx))
+    dkbc = np.zeros((ny, nx))
+    lib.orc_adr_gradient(nx, ny, prob.ns, _p(prob.solid), _p(prob.kab),
+                         _p(prob.kbc), _p(prob.ux), _p(prob.uy), _p(prob.tau),
+                         prob.flags, _p(dnds), int(xp), _p(g_steady), _p(nu),
+                         _p(dkab), _p(dkbc))
+    return dict(nu=nu, dkab=dkab, dkbc=dkbc, dNds=dnds,
+                eps=efficiency(flux, prob.ns))
+
+
+def fiber_weight_gradient(ids: np.ndarray, dkab: np.ndarray,
+                          dkbc: np.ndarray, k1: float, k2: float,
+                          nfib: int) -> np.ndarray:
+    """d eps / d w_f for relaxed weights (k_AB = w k1, k_BC = (1-w) k2 on
+    every node of fiber f): sum over its nodes of k1 dk_AB - k2 dk_BC."""
+    out = np.zeros(nfib)
+    m = ids >= 0
+    np.add.at(out, ids[m], k1 * dkab[m] - k2 * dkbc[m])
+    return out
 
 
 def residual(c_prev: np.ndarray, c: np.ndarray) -> float:

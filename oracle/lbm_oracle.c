@@ -418,3 +418,205 @@ void orc_adr_flux(int nx, int ny, int ns, const uint8_t *solid,
   }
   for (int s = 0; s < ns; ++s) flux[s] /= (double)ny;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Discrete adjoint of the ADR lattice (frozen u).                          */
+/*                                                                          */
+/* The step is affine in the pre-collision state: g' = P(K g) + b, with K    */
+/* the per-node collision + source (linear in g) and P the push streaming    */
+/* with its boundary rules (b holds the constant inlet terms).  The          */
+/* efficiency depends on the post-collision populations g* = K g on the      */
+/* flux plane through the outfluxes N_s; dNds[s] = d eps / d N_s.            */
+/* At the steady state the adjoint of the pre-collision state solves         */
+/*   nu = K^T (P^T nu + l),   l_{s,i}(x) = dNds[s] c_ix / ny on the plane,   */
+/* iterated here from nu = 0.  mu = P^T nu + l is then the adjoint of g*,    */
+/* and a rate k of solid node n enters only through the source of the links  */
+/* x -> n, so                                                                 */
+/*   d eps/d k_AB(n) = sum_{x + c_j = n} w_j C_A(x) (mu_{B,j} - mu_{A,j})(x) */
+/*   d eps/d k_BC(n) = sum_{x + c_j = n} w_j C_B(x) (mu_{C,j} - mu_{B,j})(x) */
+/* (for one species only the -mu_A term; without C only the A, B terms).     */
+/* ------------------------------------------------------------------------ */
+
+/* mu = P^T nu + l at fluid node (x, y) for species s: each post-collision
+ * population went to exactly one place in the forward push; its adjoint is
+ * read back from there. */
+static void adj_gather(int nx, int ny, int ns, const uint8_t *solid, int flags,
+                       const double *dNds, int xp, int s, int x, int y,
+                       const double *nu, double mu[Q9]) {
+  long nn = (long)nx * ny;
+  long n = (long)y * nx + x;
+  const double *v = nu + s * nn * Q9;
+  for (int i = 0; i < Q9; ++i) mu[i] = 0.0;
+  for (int i = 0; i < Q9; ++i) {
+    int tx = x + CX[i], ty = y + CY[i];
+    int io = OPP[i];
+    if (tx < 0 || tx >= nx) {
+      if (flags & ORC_PX) {
+        tx = (tx + nx) % nx;
+      } else if (tx < 0) {
+        /* inlet: g_opp = -g* + const (anti-bounce-back) or g_opp = g* */
+        if (s == 0 || (flags & ORC_INLET_ABB_ALL))
+          mu[i] += -v[n * Q9 + io];
+        else
+          mu[i] += v[n * Q9 + io];
+        continue;
+      } else {
+        /* outlet: g_opp = -g*_i + 2 w_i sum_j g*_j */
+        mu[i] += -v[n * Q9 + io];
+        for (int j = 0; j < Q9; ++j) mu[j] += 2.0 * W[i] * v[n * Q9 + io];
+        continue;
+      }
+    }
+    if (ty < 0 || ty >= ny) {
+      if (flags & ORC_PY) {
+        ty = (ty + ny) % ny;
+      } else {
+        mu[i] += v[n * Q9 + io];
+        continue;
+      }
+    }
+    long t = (long)ty * nx + tx;
+    if (solid[t])
+      mu[i] += v[n * Q9 + io];
+    else
+      mu[i] += v[t * Q9 + i];
+  }
+  if (x == xp)
+    for (int i = 0; i < Q9; ++i) mu[i] += dNds[s] * CX[i] / (double)ny;
+}
+
+/* Rates of the solid node that direction i of fluid node (x, y) points to
+ * (0 if it points to fluid, a wall, the inlet or the outlet). */
+static int link_rates(int nx, int ny, const uint8_t *solid, const double *kab,
+                      const double *kbc, int flags, int x, int y, int i,
+                      double *ka, double *kb, long *target) {
+  int tx = x + CX[i], ty = y + CY[i];
+  *ka = 0.0;
+  *kb = 0.0;
+  if (tx < 0 || tx >= nx) {
+    if (!(flags & ORC_PX)) return 0;
+    tx = (tx + nx) % nx;
+  }
+  if (ty < 0 || ty >= ny) {
+    if (!(flags & ORC_PY)) return 0;
+    ty = (ty + ny) % ny;
+  }
+  long t = (long)ty * nx + tx;
+  if (!solid[t]) return 0;
+  *ka = kab[t];
+  *kb = kbc[t];
+  *target = t;
+  return 1;
+}
+
+/* nu <- K^T (P^T nu + l), nsteps times. */
+int orc_adr_adjoint_steps(int nx, int ny, int ns, const uint8_t *solid,
+                          const double *kab, const double *kbc,
+                          const double *ux, const double *uy,
+                          const double *tau, int flags, const double *dNds,
+                          int xp, long nsteps, double *nu, double *tmp) {
+  if (ns < 1 || ns > 3 || (flags & ORC_ALLPOP)) return 1;
+  long nn = (long)nx * ny;
+  long nt = (long)ns * nn * Q9;
+  memset(tmp, 0, sizeof(double) * nt);
+  double *a = nu, *b = tmp;
+  double mu[3][Q9];
+  for (long step = 0; step < nsteps; ++step) {
+    for (int y = 0; y < ny; ++y) {
+      for (int x = 0; x < nx; ++x) {
+        long n = (long)y * nx + x;
+        if (solid[n]) continue;
+        for (int s = 0; s < ns; ++s)
+          adj_gather(nx, ny, ns, solid, flags, dNds, xp, s, x, y, a, mu[s]);
+        /* K^T: g*_{s,i} = g_{s,i} - (g_{s,i} - C_s e_i)/tau_s + Q_{s,i}(C),
+         * e_i = equilibrium(i, 1, u), C_s = sum_m g_{s,m}. */
+        double cross[3] = {0.0, 0.0, 0.0}; /* sum_{s,i} mu_{s,i} dQ_{s,i}/dC_s' */
+        for (int i = 1; i < Q9; ++i) {
+          double ka, kb;
+          long t;
+          if (!link_rates(nx, ny, solid, kab, kbc, flags, x, y, i, &ka, &kb,
+                          &t))
+            continue;
+          /* dQ_A/dC_A = -ka w, dQ_B/dC_A = +ka w, dQ_B/dC_B = -kb w,
+           * dQ_C/dC_B = +kb w (the B->C terms only with three species) */
+          cross[0] += -ka * W[i] * mu[0][i];
+          if (ns >= 2) cross[0] += ka * W[i] * mu[1][i];
+          if (ns >= 3) {
+            cross[1] += -kb * W[i] * mu[1][i];
+            cross[1] += kb * W[i] * mu[2][i];
+          }
+        }
+        for (int s = 0; s < ns; ++s) {
+          double feq_part = 0.0; /* sum_i mu_i (1/tau) e_i */
+          for (int i = 0; i < Q9; ++i)
+            feq_part += mu[s][i] * equilibrium(i, 1.0, ux[n], uy[n]) / tau[s];
+          for (int m = 0; m < Q9; ++m)
+            b[(s * nn + n) * Q9 + m] =
+                mu[s][m] * (1.0 - 1.0 / tau[s]) + feq_part + cross[s];
+        }
+      }
+    }
+    double *t = a;
+    a = b;
+    b = t;
+  }
+  if (a != nu) memcpy(nu, a, sizeof(double) * nt);
+  return 0;
+}
+
+/* Gradient of eps with respect to the rates of every solid node, from the
+ * pre-collision steady state g and the adjoint nu (see above). */
+void orc_adr_gradient(int nx, int ny, int ns, const uint8_t *solid,
+                      const double *kab, const double *kbc, const double *ux,
+                      const double *uy, const double *tau, int flags,
+                      const double *dNds, int xp, const double *g,
+                      const double *nu, double *dkab, double *dkbc) {
+  long nn = (long)nx * ny;
+  double mu[3][Q9];
+  (void)ux;
+  (void)uy;
+  (void)tau;
+  for (long n = 0; n < nn; ++n) {
+    dkab[n] = 0.0;
+    dkbc[n] = 0.0;
+  }
+  for (int y = 0; y < ny; ++y) {
+    for (int x = 0; x < nx; ++x) {
+      long n = (long)y * nx + x;
+      if (solid[n]) continue;
+      double c[3] = {0.0, 0.0, 0.0};
+      for (int s = 0; s < ns; ++s) {
+        for (int i = 0; i < Q9; ++i) c[s] += g[(s * nn + n) * Q9 + i];
+        adj_gather(nx, ny, ns, solid, flags, dNds, xp, s, x, y, nu, mu[s]);
+      }
+      for (int i = 1; i < Q9; ++i) {
+        double ka, kb;
+        long t;
+        if (!link_rates(nx, ny, solid, kab, kbc, flags, x, y, i, &ka, &kb, &t))
+          continue;
+        double da = -mu[0][i];
+        if (ns >= 2) da += mu[1][i];
+        dkab[t] += W[i] * c[0] * da;
+        if (ns >= 3) dkbc[t] += W[i] * c[1] * (mu[2][i] - mu[1][i]);
+      }
+    }
+  }
+}
+
+/* Index of the fiber that owns each node (first in list order), -1 fluid. */
+void orc_fiber_ids(int nx, int ny, int nfib, const double *fib, int32_t *ids) {
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) {
+      long n = (long)y * nx + x;
+      ids[n] = -1;
+      for (int f = 0; f < nfib; ++f) {
+        const double *p = fib + 6 * f;
+        double dx = (double)x - p[0];
+        double dy = (double)y - p[1];
+        if (dx * dx + dy * dy <= p[2] * p[2]) {
+          ids[n] = f;
+          break;
+        }
+      }
+    }
+}

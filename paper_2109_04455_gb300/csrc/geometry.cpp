@@ -46,6 +46,10 @@ extern "C" lbm_status lbm_geometry_create(int32_t nx, int32_t ny,
     g->kab.assign(np, 0.0);
     g->kbc.assign(np, 0.0);
     g->links.assign(np, kSolidNode);
+    g->fiber.assign(np, -1);
+    g->nfibers = nfibers;
+    g->k1 = k1;
+    g->k2 = k2;
 
     // Raster fiber by fiber over its bounding box; a node keeps the first
     // fiber (in list order) that contains it.
@@ -89,6 +93,7 @@ extern "C" lbm_status lbm_geometry_create(int32_t nx, int32_t ny,
           }
           g->kab[n] = a;
           g->kbc[n] = b;
+          g->fiber[n] = f;
         }
       }
     }

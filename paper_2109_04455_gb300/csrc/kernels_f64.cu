@@ -10,4 +10,9 @@ template cudaError_t launch_adr_flux<PrecF64>(int, const void *,
                                                  double *, cudaStream_t);
 template cudaError_t launch_flow<PrecF64>(int, const FlowArgs &, dim3,
                                              cudaStream_t);
+template cudaError_t launch_adjoint<PrecF64>(int, int, const AdjArgs &,
+                                                cudaStream_t);
+template cudaError_t launch_adjoint_grad<PrecF64>(
+    int, const AdjArgs &, const long long *, long long, const void *, double *,
+    double *, const int32_t *, double *, double, double, cudaStream_t);
 }  // namespace lbm

@@ -219,6 +219,8 @@ extern "C" lbm_status lbm_flow_solve(const lbm_geometry *g,
   a.nx_pad = g->nx_pad;
   a.omega = 1.0 / p->tau;
   a.u0 = p->u0;
+  a.fomega = static_cast<float>(a.omega);
+  a.fu0 = static_cast<float>(a.u0);
 
   cudaError_t e = cudaMemsetAsync(b, 0, 2 * bufb, st);
   if (e != cudaSuccess) return cuda_fail("lbm_flow_solve", e);
@@ -442,6 +444,9 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
     a.omega[k] = on ? 1.0 / p->tau[k] : 0.0;
     a.cin[k] = on ? p->c_in[k] : 0.0;
     a.cref[k] = (on && p->precision == LBM_F16DEV) ? p->c_in[k] : 0.0;
+    a.fomega[k] = static_cast<float>(a.omega[k]);
+    a.fcin[k] = static_cast<float>(a.cin[k]);
+    a.fcref[k] = static_cast<float>(a.cref[k]);
   }
   *out = s;
   return LBM_OK;
@@ -590,4 +595,216 @@ extern "C" lbm_status lbm_adr_solve(const lbm_geometry *g,
   if (info) *info = loc;
   lbm_adr_destroy(s);
   return st;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint
+// ---------------------------------------------------------------------------
+struct AdjLayout {
+  size_t buf, partials, scratch, result, fiber, total;
+};
+
+static AdjLayout adj_layout(const lbm_geometry *g, const lbm_adr_params *p) {
+  const size_t pl = static_cast<size_t>(plane_of(g));
+  const size_t ns = static_cast<size_t>(p->nspecies);
+  const dim3 gr = adr_node_grid(g->nx_pad, g->ny);
+  AdjLayout l{};
+  l.buf = align256(ns * 9 * pl * compute_bytes(p->precision));
+  l.partials = align256(static_cast<size_t>(gr.x) * gr.y * 2 * 8);
+  l.scratch = align256(kReduceGrid * 2 * 8);
+  l.result = align256(64 * 8);
+  l.fiber = align256(4 * pl);
+  l.total = 2 * l.buf + l.partials + l.scratch + l.result + l.fiber;
+  return l;
+}
+
+extern "C" size_t lbm_adr_adjoint_ws_bytes(const lbm_geometry *g,
+                                           const lbm_adr_params *p) {
+  if (!g || !p || !adr_params_ok(p) || p->precision == LBM_F16DEV) return 0;
+  return adj_layout(g, p).total;
+}
+
+static cudaError_t adj_launch(int prec, int ns, int mode, const AdjArgs &a,
+                              cudaStream_t st) {
+  return prec == LBM_F64 ? launch_adjoint<PrecF64>(ns, mode, a, st)
+                         : launch_adjoint<PrecF32>(ns, mode, a, st);
+}
+
+// d eps / d N_s of Eq. (A-B)
+static void efficiency_sensitivity(const double *f, int ns, double *d) {
+  d[0] = d[1] = d[2] = 0.0;
+  if (ns == 2) {
+    const double t = f[0] + f[1];
+    d[0] = -f[1] / (t * t);
+    d[1] = f[0] / (t * t);
+  } else if (ns == 3) {
+    const double t = f[0] + f[1] + f[2];
+    d[0] = d[1] = -f[2] / (t * t);
+    d[2] = (f[0] + f[1]) / (t * t);
+  }
+}
+
+extern "C" lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps,
+                                      double tol, int32_t check_every, void *ws,
+                                      size_t ws_bytes, void *dkab, void *dkbc,
+                                      void *dw, void *stream,
+                                      lbm_solve_info *info) {
+  if (!s || !ws || !dkab || !dkbc) {
+    set_error("lbm_adr_adjoint: NULL argument");
+    return LBM_EINVAL;
+  }
+  const lbm_geometry *g = s->g;
+  const int ns = s->p.nspecies;
+  const int prec = s->p.precision;
+  if (ns < 2 || prec == LBM_F16DEV) {
+    set_error("lbm_adr_adjoint: needs 2 or 3 species and LBM_F64 / LBM_F32");
+    return LBM_EINVAL;
+  }
+  if (!s->has_check) {
+    set_error("lbm_adr_adjoint: run the solver with info first");
+    return LBM_EINVAL;
+  }
+  if (max_steps < 1 || (tol > 0 && check_every < 2)) {
+    set_error("lbm_adr_adjoint: need max_steps >= 1 (check_every >= 2 with tol)");
+    return LBM_EINVAL;
+  }
+  if (!aligned256(ws) || !aligned256(dkab) || !aligned256(dkbc)) {
+    set_error("lbm_adr_adjoint: device buffers must be 256-byte aligned");
+    return LBM_EINVAL;
+  }
+  const AdjLayout l = adj_layout(g, &s->p);
+  if (ws_bytes < l.total) {
+    set_error("lbm_adr_adjoint: workspace too small");
+    return LBM_ENOMEM;
+  }
+  if (lbm_status bs = bind_device(ws, "lbm_adr_adjoint")) return bs;
+  cudaStream_t st = as_stream(stream);
+  char *b = static_cast<char *>(ws);
+  void *buf[2] = {b, b + l.buf};
+  double *partials = reinterpret_cast<double *>(b + 2 * l.buf);
+  double *scratch = reinterpret_cast<double *>(b + 2 * l.buf + l.partials);
+  double *result = reinterpret_cast<double *>(b + 2 * l.buf + l.partials + l.scratch);
+  int32_t *fiber = reinterpret_cast<int32_t *>(b + 2 * l.buf + l.partials +
+                                               l.scratch + l.result);
+  const size_t pl = static_cast<size_t>(plane_of(g));
+  const dim3 gr = adr_node_grid(g->nx_pad, g->ny);
+  const long long rows = static_cast<long long>(gr.x) * gr.y;
+
+  // forward outfluxes of the current state -> d eps / d N_s
+  cudaError_t e = adr_flux_launch(s, st);
+  double h[16] = {0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h, s->result, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_adjoint(flux)", e);
+  double flux[3] = {h[8], h[9], h[10]};
+  double dN[3];
+  efficiency_sensitivity(flux, ns, dN);
+  if (!std::isfinite(dN[0]) || !std::isfinite(dN[1]) || !std::isfinite(dN[2])) {
+    set_error("lbm_adr_adjoint: efficiency undefined (zero outflux)");
+    return LBM_EUNSTABLE;
+  }
+
+  AdjArgs a{};
+  a.links = g->d_links;
+  a.kab = g->d_kab;
+  a.kbc = g->d_kbc;
+  a.u = s->a.u;
+  a.partials = partials;
+  a.plane = plane_of(g);
+  a.nx = g->nx;
+  a.ny = g->ny;
+  a.nx_pad = g->nx_pad;
+  a.xp = s->p.x_plane < 0 ? g->nx - 3 : s->p.x_plane;
+  a.abb_all = s->a.abb_all;
+  for (int k = 0; k < 3; ++k) {
+    a.omega[k] = s->a.omega[k];
+    a.dN[k] = dN[k];
+    a.fomega[k] = static_cast<float>(a.omega[k]);
+    a.fdN[k] = static_cast<float>(dN[k]);
+  }
+  e = cudaMemsetAsync(b, 0, 2 * l.buf, st);
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_adjoint", e);
+  int cur = 0;
+  int64_t steps = 0;
+  double residual = INFINITY;
+  bool converged = false;
+  auto iterate = [&](int64_t n) -> lbm_status {
+    for (int64_t k = 0; k < n; ++k) {
+      a.src = buf[cur];
+      a.dst = buf[cur ^ 1];
+      const int mode = (k == n - 1) ? kAdjCheck : kAdjStep;
+      cudaError_t e2 = adj_launch(prec, ns, mode, a, st);
+      if (e2 != cudaSuccess) return cuda_fail("lbm_adr_adjoint(step)", e2);
+      cur ^= 1;
+      ++steps;
+    }
+    cudaError_t e2 = launch_reduce(2, partials, rows, scratch, result, st);
+    double r[2] = {0, 0};
+    if (e2 == cudaSuccess)
+      e2 = cudaMemcpyAsync(r, result, sizeof(r), cudaMemcpyDeviceToHost, st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) return cuda_fail("lbm_adr_adjoint(check)", e2);
+    if (!std::isfinite(r[0]) || !std::isfinite(r[1])) {
+      set_error("lbm_adr_adjoint: non-finite adjoint");
+      return LBM_EUNSTABLE;
+    }
+    residual = r[1] > 0 ? r[0] / r[1] : 0.0;
+    return LBM_OK;
+  };
+  lbm_status stt = LBM_OK;
+  if (tol <= 0) {
+    stt = iterate(max_steps);
+  } else {
+    while (stt == LBM_OK) {
+      const int64_t left = max_steps - steps;
+      stt = iterate(left < check_every ? left : check_every);
+      if (stt != LBM_OK) break;
+      if (residual < tol) {
+        converged = true;
+        break;
+      }
+      if (steps >= max_steps) {
+        set_error("lbm_adr_adjoint: not converged within max_steps");
+        stt = LBM_ENOTCONVERGED;
+      }
+    }
+  }
+  if (stt == LBM_OK || stt == LBM_ENOTCONVERGED) {
+    // gradients from the final adjoint and the recorded concentrations
+    e = cudaMemsetAsync(dkab, 0, 8 * pl, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dkbc, 0, 8 * pl, st);
+    if (e == cudaSuccess && dw && g->nfibers > 0)
+      e = cudaMemsetAsync(dw, 0, 8 * static_cast<size_t>(g->nfibers), st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(fiber, g->fiber.data(), 4 * pl, cudaMemcpyHostToDevice, st);
+    a.src = buf[cur];
+    a.dst = nullptr;
+    const long long nbnd = static_cast<long long>(g->bnodes.size());
+    if (e == cudaSuccess) {
+      e = prec == LBM_F64
+              ? launch_adjoint_grad<PrecF64>(ns, a, g->d_bnodes, nbnd, s->cprev,
+                                             static_cast<double *>(dkab),
+                                             static_cast<double *>(dkbc), fiber,
+                                             static_cast<double *>(dw), g->k1,
+                                             g->k2, st)
+              : launch_adjoint_grad<PrecF32>(ns, a, g->d_bnodes, nbnd, s->cprev,
+                                             static_cast<double *>(dkab),
+                                             static_cast<double *>(dkbc), fiber,
+                                             static_cast<double *>(dw), g->k1,
+                                             g->k2, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail("lbm_adr_adjoint(gradient)", e);
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->steps = steps;
+    info->residual = residual;
+    info->converged = converged ? 1 : 0;
+    for (int k = 0; k < 3; ++k) info->flux[k] = flux[k];
+    double eps = 0.0;
+    if (lbm_efficiency(flux, ns, &eps) == LBM_OK) info->eps = eps;
+  }
+  return stt;
 }

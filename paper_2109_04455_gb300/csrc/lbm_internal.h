@@ -43,6 +43,9 @@ struct lbm_geometry {
   std::vector<double> kab, kbc;   // [ny][nx_pad]
   std::vector<uint32_t> links;    // [ny][nx_pad]
   std::vector<long long> bnodes;  // fluid nodes with a non-zero link word
+  std::vector<int32_t> fiber;     // [ny][nx_pad] owning fiber, -1 elsewhere
+  int32_t nfibers = 0;
+  double k1 = 0.0, k2 = 0.0;
   // device copies (borrowed from the caller's workspace after upload)
   const uint32_t *d_links = nullptr;
   const long long *d_bnodes = nullptr;

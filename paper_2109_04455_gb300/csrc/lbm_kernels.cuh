@@ -126,6 +126,19 @@ __device__ __forceinline__ S zero_of() { return S(0); }
 template <>
 __device__ __forceinline__ __half zero_of<__half>() { return __float2half_rn(0.0f); }
 
+// Kernel parameters come in double and in float; the float paths read the
+// float copy, so no thread converts a double (this part's FP64 pipe is
+// narrow enough for per-thread conversions to show up in a step's time).
+template <typename T>
+__device__ __forceinline__ T pick(double d, float f);
+template <>
+__device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+__device__ __forceinline__ float absT(float x) { return fabsf(x); }
+__device__ __forceinline__ double absT(double x) { return fabs(x); }
+
 // ---------------------------------------------------------------------------
 // ADR
 // ---------------------------------------------------------------------------
@@ -146,6 +159,7 @@ struct AdrArgs {
   double omega[3];          // 1/tau per species
   double cin[3];            // inlet concentration per species
   double cref[3];           // reference concentration of the stored deviation
+  float fomega[3], fcin[3], fcref[3];  // the same in float
 };
 
 enum AdrMode { kAdrStep = 0, kAdrCheck = 1, kAdrInit = 2 };
@@ -154,7 +168,7 @@ enum AdrMode { kAdrStep = 0, kAdrCheck = 1, kAdrInit = 2 };
 template <class P>
 __device__ __forceinline__ typename P::T adr_shift(const AdrArgs &a, int s, int i) {
   using T = typename P::T;
-  return P::kDev ? Lattice<T>::w(i) * T(a.cref[s]) : T(0);
+  return P::kDev ? Lattice<T>::w(i) * pick<T>(a.cref[s], a.fcref[s]) : T(0);
 }
 
 template <class P>
@@ -200,7 +214,8 @@ __device__ __forceinline__ void adr_boundary(const AdrArgs &a, int s,
     if (t == kFluid) continue;
     const T back = adr_ld<P>(a, s, opp(i), n);
     if (t == kInlet) {
-      g[i] = (s == 0 || a.abb_all) ? -back + T(2) * Lattice<T>::w(i) * T(a.cin[s])
+      g[i] = (s == 0 || a.abb_all)
+                 ? -back + T(2) * Lattice<T>::w(i) * pick<T>(a.cin[s], a.fcin[s])
                                    : back;
     } else if (t == kOutlet) {
       g[i] = -back + T(2) * Lattice<T>::w(i) * cb;
@@ -225,7 +240,7 @@ __device__ __forceinline__ typename P::T adr_collide(const AdrArgs &a, int s,
 #pragma unroll
   for (int i = 0; i < 9; ++i) c += g[i];
   C[s] = c;
-  const T om = T(a.omega[s]);
+  const T om = pick<T>(a.omega[s], a.fomega[s]);
 #pragma unroll
   for (int i = 0; i < 9; ++i) g[i] = g[i] + om * (c * E[i] - g[i]);
   if (lw != 0u) {
@@ -306,8 +321,8 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
         dst[(long long)(s * 9 + i) * plane + n] = P::store(g[i] - adr_shift<P>(a, s, i));
       if (MODE == kAdrCheck) {
         T *cp = static_cast<T *>(a.cprev);
-        acc[2 * s] = fabs(c - cp[s * plane + n]);
-        acc[2 * s + 1] = fabs(c);
+        acc[2 * s] = absT(c - cp[s * plane + n]);
+        acc[2 * s + 1] = absT(c);
         cp[s * plane + n] = c;
       }
     }
@@ -325,112 +340,154 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
   }
 }
 
-// Bulk step, two nodes per thread (x0 = 2 t, x0 + 1): the interior formula
-// (pull from x - c_i, BGK, no source) for every fluid node, without looking
-// at link types, so the kernel has no per-direction branches.  Boundary
-// nodes get a provisional value here that adr_node_kernel<..., LIST = true>
-// overwrites right after; their residual terms and C are left to that kernel.
-// Each population plane is read with aligned two-wide vector loads; the
-// neighbour element a horizontal or diagonal pull needs (x0 - 1 or x0 + 2)
-// comes from the adjacent lane by a warp shuffle, and only the first / last
-// lane of a warp issues one extra scalar load for it.  Reads outside the
-// lattice rows or row ends are skipped (zeros), so every access stays in
-// bounds.  Stores are two-wide and aligned.
-template <class P, int NS, int MODE>
+// Bulk step: the interior formula (pull from x - c_i, BGK, no source) for
+// the nodes whose eight neighbours are all fluid (link word 0); every other
+// node is left to adr_node_kernel<..., LIST = true>, launched right after.
+// All populations of all species are loaded before any arithmetic, so a
+// thread keeps NS*9 independent loads in flight.  VEC = 2 gives each thread
+// two nodes (x0 = 2t, x0 + 1): every plane is read with aligned two-wide
+// vector loads, the element a horizontal or diagonal pull needs from the
+// next pair over (x0 - 1 or x0 + 2) comes from the adjacent lane by a warp
+// shuffle, and only the first / last lane of a warp loads it itself.  Reads
+// outside the lattice rows or row ends are skipped, so all accesses stay in
+// bounds; their values only reach nodes the boundary kernel rewrites.
+template <class P, int NS, int MODE, int VEC>
 __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
     adr_bulk_kernel(const AdrArgs a) {
   using S = typename P::S;
   using T = typename P::T;
-  using VS = typename Vec2<S>::type;
-  using VT = typename Vec2<T>::type;
-  const int lane = threadIdx.x & 31;
-  const int x0 = 2 * (blockIdx.x * kBlockX + threadIdx.x);
-  const int y = blockIdx.y;
   const long long np = a.nx_pad, plane = a.plane;
-  const bool valid = x0 < a.nx_pad;  // nx_pad is even: x0 + 1 is inside too
-  const long long n0 = (long long)y * np + x0;
+  const int y = blockIdx.y;
   const S *__restrict__ src = static_cast<const S *>(a.src);
   S *__restrict__ dst = static_cast<S *>(a.dst);
-
-  uint2 lw = make_uint2(kSolidNode, kSolidNode);
-  VT ux = {T(0), T(0)}, uy = {T(0), T(0)};
-  if (valid) {
-    lw = *reinterpret_cast<const uint2 *>(a.links + n0);
-    const T *U = static_cast<const T *>(a.u);
-    ux = *reinterpret_cast<const VT *>(U + n0);
-    uy = *reinterpret_cast<const VT *>(U + plane + n0);
-  }
-  const bool fluid0 = lw.x != kSolidNode, fluid1 = lw.y != kSolidNode;
-  const bool inner0 = lw.x == 0u, inner1 = lw.y == 0u;
-  T E0[9], E1[9];
-  eq_factors<T>(ux.x, uy.x, E0);
-  eq_factors<T>(ux.y, uy.y, E1);
-
+  const T *__restrict__ U = static_cast<const T *>(a.u);
   T acc[2 * NS];
 #pragma unroll
   for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
 
+  if (VEC == 1) {
+    const int x = blockIdx.x * kBlockX + threadIdx.x;
+    const long long n = (long long)y * np + x;
+    const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
+    if (lw == 0u) {
+      T g[NS][9];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    T g0[9], g1[9];
+      for (int s = 0; s < NS; ++s) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int row = y - cy(i);
-      const bool rowok = valid && row >= 0 && row < a.ny;
-      const long long base = (long long)(s * 9 + i) * plane + (long long)row * np + x0;
-      S e0 = zero_of<S>(), e1 = zero_of<S>();
-      if (rowok) {
-        const VS v = *reinterpret_cast<const VS *>(src + base);
-        e0 = v.x;
-        e1 = v.y;
+        for (int i = 0; i < 9; ++i)
+          g[s][i] = P::load(src[(long long)(s * 9 + i) * plane + n - (cy(i) * np + cx(i))]) +
+                    adr_shift<P>(a, s, i);
       }
-      S lo, hi;
-      if (cx(i) == 0) {
-        lo = e0;
-        hi = e1;
-      } else if (cx(i) > 0) {  // sources x0 - 1, x0
-        S left = __shfl_up_sync(0xffffffffu, e1, 1);
-        if (lane == 0) left = (rowok && x0 >= 1) ? src[base - 1] : zero_of<S>();
-        lo = left;
-        hi = e0;
-      } else {  // sources x0 + 1, x0 + 2
-        S right = __shfl_down_sync(0xffffffffu, e0, 1);
-        if (lane == 31) right = (rowok && x0 + 2 < a.nx_pad) ? src[base + 2] : zero_of<S>();
-        lo = e1;
-        hi = right;
-      }
-      const T sh = adr_shift<P>(a, s, i);
-      g0[i] = P::load(lo) + sh;
-      g1[i] = P::load(hi) + sh;
-    }
-
-    T c0 = T(0), c1 = T(0);
+      T E[9];
+      eq_factors<T>(U[n], U[plane + n], E);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      c0 += g0[i];
-      c1 += g1[i];
+      for (int s = 0; s < NS; ++s) {
+        T c = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) c += g[s][i];
+        const T om = pick<T>(a.omega[s], a.fomega[s]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          dst[(long long)(s * 9 + i) * plane + n] =
+              P::store(g[s][i] + om * (c * E[i] - g[s][i]) - adr_shift<P>(a, s, i));
+        if (MODE == kAdrCheck) {
+          T *cp = static_cast<T *>(a.cprev);
+          acc[2 * s] = absT(c - cp[s * plane + n]);
+          acc[2 * s + 1] = absT(c);
+          cp[s * plane + n] = c;
+        }
+      }
     }
-    const T om = T(a.omega[s]);
-    if (valid) {
+  } else {
+    using VS = typename Vec2<S>::type;
+    using VT = typename Vec2<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int x0 = 2 * (blockIdx.x * kBlockX + threadIdx.x);
+    const bool valid = x0 < a.nx_pad;  // nx_pad is even: x0 + 1 is inside too
+    const long long n0 = (long long)y * np + x0;
+    uint2 lw = make_uint2(kSolidNode, kSolidNode);
+    if (valid) lw = *reinterpret_cast<const uint2 *>(a.links + n0);
+    const bool in0 = lw.x == 0u, in1 = lw.y == 0u;
+    T g0[NS][9], g1[NS][9];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        const T sh = adr_shift<P>(a, s, i);
-        VS v;   // solid / padding nodes store zeros (never read)
-        v.x = fluid0 ? P::store(g0[i] + om * (c0 * E0[i] - g0[i]) - sh) : zero_of<S>();
-        v.y = fluid1 ? P::store(g1[i] + om * (c1 * E1[i] - g1[i]) - sh) : zero_of<S>();
-        *reinterpret_cast<VS *>(dst + (long long)(s * 9 + i) * plane + n0) = v;
-      }
-      if (MODE == kAdrCheck) {
-        T *cp = static_cast<T *>(a.cprev) + s * plane + n0;
-        if (inner0) {
-          acc[2 * s] += fabs(c0 - cp[0]);
-          acc[2 * s + 1] += fabs(c0);
-          cp[0] = c0;
+        const int row = y - cy(i);
+        const bool rowok = valid && row >= 0 && row < a.ny;
+        const long long base = (long long)(s * 9 + i) * plane + (long long)row * np + x0;
+        S e0 = zero_of<S>(), e1 = zero_of<S>();
+        if (rowok) {
+          const VS v = *reinterpret_cast<const VS *>(src + base);
+          e0 = v.x;
+          e1 = v.y;
         }
-        if (inner1) {
-          acc[2 * s] += fabs(c1 - cp[1]);
-          acc[2 * s + 1] += fabs(c1);
-          cp[1] = c1;
+        S lo, hi;
+        if (cx(i) == 0) {
+          lo = e0;
+          hi = e1;
+        } else if (cx(i) > 0) {  // sources x0 - 1, x0
+          S left = __shfl_up_sync(0xffffffffu, e1, 1);
+          if (lane == 0) left = (rowok && x0 >= 1) ? src[base - 1] : zero_of<S>();
+          lo = left;
+          hi = e0;
+        } else {  // sources x0 + 1, x0 + 2
+          S right = __shfl_down_sync(0xffffffffu, e0, 1);
+          if (lane == 31) right = (rowok && x0 + 2 < a.nx_pad) ? src[base + 2] : zero_of<S>();
+          lo = e1;
+          hi = right;
+        }
+        const T sh = adr_shift<P>(a, s, i);
+        g0[s][i] = P::load(lo) + sh;
+        g1[s][i] = P::load(hi) + sh;
+      }
+    }
+    if (valid && (in0 || in1)) {
+      const VT ux = *reinterpret_cast<const VT *>(U + n0);
+      const VT uy = *reinterpret_cast<const VT *>(U + plane + n0);
+      T E0[9], E1[9];
+      eq_factors<T>(ux.x, uy.x, E0);
+      eq_factors<T>(ux.y, uy.y, E1);
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        T c0 = T(0), c1 = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          c0 += g0[s][i];
+          c1 += g1[s][i];
+        }
+        const T om = pick<T>(a.omega[s], a.fomega[s]);
+        if (in0 && in1) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            const T sh = adr_shift<P>(a, s, i);
+            VS v;
+            v.x = P::store(g0[s][i] + om * (c0 * E0[i] - g0[s][i]) - sh);
+            v.y = P::store(g1[s][i] + om * (c1 * E1[i] - g1[s][i]) - sh);
+            *reinterpret_cast<VS *>(dst + (long long)(s * 9 + i) * plane + n0) = v;
+          }
+        } else {
+          // one interior node: scalar stores, the other node is not touched
+#pragma unroll
+          for (int i = 0; i < 9; ++i) {
+            const T sh = adr_shift<P>(a, s, i);
+            const long long o = (long long)(s * 9 + i) * plane + n0;
+            if (in0) dst[o] = P::store(g0[s][i] + om * (c0 * E0[i] - g0[s][i]) - sh);
+            if (in1) dst[o + 1] = P::store(g1[s][i] + om * (c1 * E1[i] - g1[s][i]) - sh);
+          }
+        }
+        if (MODE == kAdrCheck) {
+          T *cp = static_cast<T *>(a.cprev) + s * plane + n0;
+          if (in0) {
+            acc[2 * s] += absT(c0 - cp[0]);
+            acc[2 * s + 1] += absT(c0);
+            cp[0] = c0;
+          }
+          if (in1) {
+            acc[2 * s] += absT(c1 - cp[1]);
+            acc[2 * s + 1] += absT(c1);
+            cp[1] = c1;
+          }
         }
       }
     }
@@ -510,6 +567,183 @@ __global__ void __launch_bounds__(kReduceThreads)
 }
 
 // ---------------------------------------------------------------------------
+// discrete adjoint of the ADR step (frozen u)
+//
+// The step is affine in the stored state: g*(t+1) = K (P g*(t) + b), with P
+// the pull and its link rules, K the per-node collision + source.  The
+// efficiency depends on g* on the flux plane through N_s (dN[s] = d eps/dN_s).
+// The adjoint of the pre-collision populations solves
+//   nu = K^T (P^T nu + l),   l_{s,i}(x) = dN[s] c_ix / ny on the plane,
+// iterated from nu = 0.  P^T is a gather in the opposite direction of the
+// forward pull: the value pulled by neighbour x + c_i is read back from it,
+// a bounced population from the node's own opposite direction.  K^T is
+// local and cheap: nu'_{s,m} = (1 - w_s) mu_{s,m} + w_s sum_i E_i mu_{s,i}
+// + R_s, with R_A = sum_j w_j k_AB (mu_B - mu_A)_j and
+// R_B = sum_j w_j k_BC (mu_C - mu_B)_j over the catalytic links j.
+// ---------------------------------------------------------------------------
+struct AdjArgs {
+  const void *src;          // T [ns][9][plane]  nu at iteration t
+  void *dst;                // T [ns][9][plane]  nu at iteration t+1
+  const uint32_t *links;
+  const double *kab, *kbc;
+  const void *u;            // T [2][plane]
+  double *partials;         // [rows][2]  (check iterations)
+  long long plane;
+  int nx, ny, nx_pad, xp;
+  int abb_all;
+  double omega[3];
+  double dN[3];             // d eps / d N_s
+  float fomega[3], fdN[3];  // the same in float
+};
+
+enum AdjMode { kAdjStep = 0, kAdjCheck = 1 };
+
+// mu = P^T nu + l of species s at fluid node n (link word lw)
+template <typename T>
+__device__ __forceinline__ void adj_gather(const AdjArgs &a, int s, uint32_t lw,
+                                           long long n, int x, T (&mu)[9]) {
+  const T *nu = static_cast<const T *>(a.src) + (long long)s * 9 * a.plane;
+  const long long np = a.nx_pad, plane = a.plane;
+  mu[0] = nu[n];
+  T outlet = T(0);
+#pragma unroll
+  for (int i = 1; i < 9; ++i) {
+    const uint32_t t = lw == 0u ? (uint32_t)kFluid : nib(lw, i);
+    if (t == kFluid) {
+      mu[i] = nu[(long long)i * plane + n + cy(i) * np + cx(i)];
+    } else {
+      const T back = nu[(long long)opp(i) * plane + n];
+      if (t == kInlet) {
+        mu[i] = (s == 0 || a.abb_all) ? -back : back;
+      } else if (t == kOutlet) {
+        mu[i] = -back;
+        outlet += T(2) * Lattice<T>::w(opp(i)) * back;
+      } else {
+        mu[i] = back;
+      }
+    }
+  }
+  if (outlet != T(0)) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mu[i] += outlet;
+  }
+  if (x == a.xp) {
+    const T d = pick<T>(a.dN[s], a.fdN[s]) / T(a.ny);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) mu[i] += T(cx(i)) * d;
+  }
+}
+
+template <typename T, int NS, int MODE>
+__global__ void __launch_bounds__(kBlockX) adj_kernel(const AdjArgs a) {
+  const int x = blockIdx.x * kBlockX + threadIdx.x;
+  const int y = blockIdx.y;
+  const long long n = (long long)y * a.nx_pad + x;
+  const long long plane = a.plane;
+  const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
+  T acc[2] = {T(0), T(0)};
+  if (lw != kSolidNode) {
+    const T *U = static_cast<const T *>(a.u);
+    T E[9];
+    eq_factors<T>(U[n], U[plane + n], E);
+    T mu[NS][9];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) adj_gather<T>(a, s, lw, n, x, mu[s]);
+    T R[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) R[s] = T(0);
+    if (lw != 0u) {
+      const long long np = a.nx_pad;
+#pragma unroll
+      for (int j = 1; j < 9; ++j) {
+        if (nib(lw, j) != kCat) continue;
+        const long long m = n + cy(j) * np + cx(j);
+        const T wj = Lattice<T>::w(j);
+        const T ka = T(a.kab[m]) * wj;
+        R[0] += ka * ((NS >= 2 ? mu[NS >= 2 ? 1 : 0][j] : T(0)) - mu[0][j]);
+        if (NS >= 3) {
+          const T kb = T(a.kbc[m]) * wj;
+          R[NS >= 3 ? 1 : 0] += kb * (mu[NS >= 3 ? 2 : 0][j] - mu[NS >= 3 ? 1 : 0][j]);
+        }
+      }
+    }
+    T *dst = static_cast<T *>(a.dst);
+    const T *src = static_cast<const T *>(a.src);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const T om = pick<T>(a.omega[s], a.fomega[s]);
+      T lam = T(0);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) lam += E[i] * mu[s][i];
+      lam = om * lam + R[s];
+#pragma unroll
+      for (int m = 0; m < 9; ++m) {
+        const T v = (T(1) - om) * mu[s][m] + lam;
+        const long long idx = (long long)(s * 9 + m) * plane + n;
+        if (MODE == kAdjCheck) {
+          acc[0] += absT(v - src[idx]);
+          acc[1] += absT(v);
+        }
+        dst[idx] = v;
+      }
+    }
+  }
+  if (MODE == kAdjCheck) {
+    double tot[2];
+    block_sum<2, T>(acc, tot);
+    if (threadIdx.x == 0) {
+      const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+      a.partials[b * 2] = tot[0];
+      a.partials[b * 2 + 1] = tot[1];
+    }
+  }
+}
+
+// Rate gradients from the adjoint (a.src = nu) and the pre-collision
+// concentrations C (the forward solver's last checked step), over the
+// boundary nodes; each link x -> n into a fiber node adds
+//   d eps/dk_AB(n) += w_j C_A(x) (mu_B - mu_A)_j,
+//   d eps/dk_BC(n) += w_j C_B(x) (mu_C - mu_B)_j,
+// and, when fiber ids are given, d eps/dw_f += k1 (first) - k2 (second).
+template <typename T, int NS>
+__global__ void __launch_bounds__(kBlockX)
+    adj_grad_kernel(const AdjArgs a, const long long *bnodes, long long nbnd,
+                    const T *conc, double *dkab, double *dkbc,
+                    const int32_t *fiber, double *dw, double k1, double k2) {
+  const long long t = (long long)blockIdx.x * kBlockX + threadIdx.x;
+  if (t >= nbnd) return;
+  const long long n = bnodes[t];
+  const uint32_t lw = a.links[n];
+  const int x = static_cast<int>(n % a.nx_pad);
+  T mu[NS][9];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) adj_gather<T>(a, s, lw, n, x, mu[s]);
+  const T cA = conc[n];
+  const T cB = NS >= 2 ? conc[a.plane + n] : T(0);
+  const long long np = a.nx_pad;
+#pragma unroll
+  for (int j = 1; j < 9; ++j) {
+    const uint32_t ty = nib(lw, j);
+    if (ty != kCat && ty != kInert) continue;
+    const long long m = n + cy(j) * np + cx(j);
+    const double wj = double(Lattice<T>::w(j));
+    double ga = -double(mu[0][j]);
+    if (NS >= 2) ga += double(mu[NS >= 2 ? 1 : 0][j]);
+    ga *= wj * double(cA);
+    double gb = 0.0;
+    if (NS >= 3)
+      gb = wj * double(cB) *
+           (double(mu[NS >= 3 ? 2 : 0][j]) - double(mu[NS >= 3 ? 1 : 0][j]));
+    atomicAdd(dkab + m, ga);
+    if (NS >= 3) atomicAdd(dkbc + m, gb);
+    if (fiber != nullptr && dw != nullptr) {
+      const int f = fiber[m];
+      if (f >= 0) atomicAdd(dw + f, k1 * ga - k2 * gb);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // flow
 // ---------------------------------------------------------------------------
 struct FlowArgs {
@@ -522,6 +756,7 @@ struct FlowArgs {
   int nx, ny, nx_pad;
   double omega;           // 1/tau
   double u0;              // inflow centreline velocity
+  float fomega, fu0;      // the same in float
 };
 
 enum FlowMode { kFlowStep = 0, kFlowU = 1, kFlowCheck = 2, kFlowInit = 3 };
@@ -547,7 +782,7 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
     };
     // inflow parabola at this row, zeros half a node outside the walls
     const T yy = T(y);
-    const T uin = T(4) * T(a.u0) * (yy + T(0.5)) * (T(a.ny) - T(0.5) - yy) /
+    const T uin = T(4) * pick<T>(a.u0, a.fu0) * (yy + T(0.5)) * (T(a.ny) - T(0.5) - yy) /
                   (T(a.ny) * T(a.ny));
 
     T f[9];
@@ -607,7 +842,7 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
     }
     const T ux = jx / rho, uy = jy / rho;
     const T uu = ux * ux + uy * uy;
-    const T om = T(a.omega);
+    const T om = pick<T>(a.omega, a.fomega);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const T cu = T(cx(i)) * ux + T(cy(i)) * uy;
@@ -617,8 +852,8 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
     }
     if (MODE == kFlowU || MODE == kFlowCheck) {
       if (MODE == kFlowCheck) {
-        acc[0] = fabs(ux - U[n]) + fabs(uy - U[plane + n]);
-        acc[1] = fabs(ux) + fabs(uy);
+        acc[0] = absT(ux - U[n]) + absT(uy - U[plane + n]);
+        acc[1] = absT(ux) + absT(uy);
       }
       U[n] = ux;
       U[plane + n] = uy;
@@ -648,8 +883,13 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
 #ifndef LBM_ADR_SPLIT
 #define LBM_ADR_SPLIT 1
 #endif
+// nodes per thread of the bulk kernel (1 or 2)
+#ifndef LBM_ADR_VEC
+#define LBM_ADR_VEC 1
+#endif
 inline dim3 adr_bulk_grid(int nx_pad, int ny) {
-  return dim3(static_cast<unsigned>((nx_pad + 2 * kBlockX - 1) / (2 * kBlockX)),
+  const int per = LBM_ADR_VEC * kBlockX;
+  return dim3(static_cast<unsigned>((nx_pad + per - 1) / per),
               static_cast<unsigned>(ny));
 }
 inline dim3 adr_node_grid(int nx_pad, int ny) {
@@ -677,6 +917,13 @@ cudaError_t launch_adr_flux(int ns, const void *g, const uint32_t *links,
                             const double *cref, double *out, cudaStream_t st);
 template <class P>
 cudaError_t launch_flow(int mode, const FlowArgs &a, dim3 grid, cudaStream_t st);
+template <class P>
+cudaError_t launch_adjoint(int ns, int mode, const AdjArgs &a, cudaStream_t st);
+template <class P>
+cudaError_t launch_adjoint_grad(int ns, const AdjArgs &a, const long long *bnodes,
+                                long long nbnd, const void *conc, double *dkab,
+                                double *dkbc, const int32_t *fiber, double *dw,
+                                double k1, double k2, cudaStream_t st);
 
 // Two-level deterministic sum of nb rows of k partials into out[0..k);
 // scratch holds kReduceGrid * k doubles.

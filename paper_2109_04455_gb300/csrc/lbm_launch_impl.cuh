@@ -29,10 +29,10 @@ static cudaError_t launch_adr_ns(int mode, const AdrArgs &a, cudaStream_t st) {
   b.part_off = static_cast<long long>(bg.x) * bg.y;
   const unsigned lb = static_cast<unsigned>(adr_list_blocks(a.nbnd));
   if (mode == kAdrStep) {
-    adr_bulk_kernel<P, NS, kAdrStep><<<bg, block, 0, st>>>(a);
+    adr_bulk_kernel<P, NS, kAdrStep, LBM_ADR_VEC><<<bg, block, 0, st>>>(a);
     if (lb) adr_node_kernel<P, NS, kAdrStep, true><<<lb, block, 0, st>>>(b);
   } else {
-    adr_bulk_kernel<P, NS, kAdrCheck><<<bg, block, 0, st>>>(a);
+    adr_bulk_kernel<P, NS, kAdrCheck, LBM_ADR_VEC><<<bg, block, 0, st>>>(a);
     if (lb) adr_node_kernel<P, NS, kAdrCheck, true><<<lb, block, 0, st>>>(b);
   }
   return cudaGetLastError();
@@ -76,6 +76,45 @@ cudaError_t launch_flow(int mode, const FlowArgs &a, dim3 grid,
     case kFlowU: flow_kernel<P, kFlowU><<<grid, block, 0, st>>>(a); break;
     case kFlowCheck: flow_kernel<P, kFlowCheck><<<grid, block, 0, st>>>(a); break;
     case kFlowInit: flow_kernel<P, kFlowInit><<<grid, block, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t launch_adjoint(int ns, int mode, const AdjArgs &a, cudaStream_t st) {
+  using T = typename P::T;
+  const dim3 block(kBlockX);
+  const dim3 grid = adr_node_grid(a.nx_pad, a.ny);
+#define LBM_ADJ_CASE(NS)                                                  \
+  if (ns == NS) {                                                         \
+    if (mode == kAdjCheck)                                                \
+      adj_kernel<T, NS, kAdjCheck><<<grid, block, 0, st>>>(a);            \
+    else                                                                  \
+      adj_kernel<T, NS, kAdjStep><<<grid, block, 0, st>>>(a);             \
+    return cudaGetLastError();                                            \
+  }
+  LBM_ADJ_CASE(1)
+  LBM_ADJ_CASE(2)
+  LBM_ADJ_CASE(3)
+#undef LBM_ADJ_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <class P>
+cudaError_t launch_adjoint_grad(int ns, const AdjArgs &a, const long long *bnodes,
+                                long long nbnd, const void *conc, double *dkab,
+                                double *dkbc, const int32_t *fiber, double *dw,
+                                double k1, double k2, cudaStream_t st) {
+  using T = typename P::T;
+  if (nbnd == 0) return cudaSuccess;
+  const dim3 block(kBlockX);
+  const unsigned nb = static_cast<unsigned>(adr_list_blocks(nbnd));
+  const T *c = static_cast<const T *>(conc);
+  switch (ns) {
+    case 1: adj_grad_kernel<T, 1><<<nb, block, 0, st>>>(a, bnodes, nbnd, c, dkab, dkbc, fiber, dw, k1, k2); break;
+    case 2: adj_grad_kernel<T, 2><<<nb, block, 0, st>>>(a, bnodes, nbnd, c, dkab, dkbc, fiber, dw, k1, k2); break;
+    case 3: adj_grad_kernel<T, 3><<<nb, block, 0, st>>>(a, bnodes, nbnd, c, dkab, dkbc, fiber, dw, k1, k2); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -84,6 +84,10 @@ _SIGS = {
     "lbm_adr_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_size_t, _P, _P,
                                      _P]),
     "lbm_efficiency": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "lbm_adr_adjoint_ws_bytes": (ctypes.c_size_t, [_P, _P]),
+    "lbm_adr_adjoint": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double,
+                                       ctypes.c_int32, _P, ctypes.c_size_t,
+                                       _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -274,6 +278,51 @@ class ADRSolver:
         _check(load().lbm_adr_conc(self.handle, ctypes.c_void_p(c.data_ptr()),
                                    _stream_ptr(stream)))
         return c
+
+    def adjoint(self, max_steps: int, tol: float = 0.0,
+                check_every: int = 100, nfibers: int = 0, stream=None,
+                raise_not_converged: bool = False):
+        """lbm_adr_adjoint at the current state; returns (dkab, dkbc, dw,
+        info) with dkab/dkbc [ny, nx_pad] float64 on the device and dw
+        [nfibers] (None if nfibers == 0)."""
+        import torch
+        lib = load()
+        dev = self.geom.ws.device
+        ws = _device_bytes(lib.lbm_adr_adjoint_ws_bytes(
+            self.geom.handle, ctypes.byref(self.params)), dev)
+        shape = (self.geom.ny, self.geom.nx_pad)
+        dkab = torch.empty(shape, dtype=torch.float64, device=dev)
+        dkbc = torch.empty(shape, dtype=torch.float64, device=dev)
+        dw = (torch.empty(nfibers, dtype=torch.float64, device=dev)
+              if nfibers > 0 else None)
+        info = lbm_solve_info()
+        st = lib.lbm_adr_adjoint(self.handle, int(max_steps), tol,
+                                 int(check_every),
+                                 ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                 ctypes.c_void_p(dkab.data_ptr()),
+                                 ctypes.c_void_p(dkbc.data_ptr()),
+                                 ctypes.c_void_p(dw.data_ptr())
+                                 if dw is not None else None,
+                                 _stream_ptr(stream), ctypes.byref(info))
+        if st != LBM_OK and not (st == LBM_ENOTCONVERGED and
+                                 not raise_not_converged):
+            _check(st)
+        return dkab, dkbc, dw, info.as_dict()
+
+    def solve(self, tol: float, check_every: int, max_steps: int,
+              stream=None):
+        """Run in chunks of check_every until the residual is below tol (or
+        max_steps); returns the last info (converged flag inside)."""
+        info = None
+        done = 0
+        while done < max_steps:
+            n = min(check_every, max_steps - done)
+            info = self.run(max(n, 2), stream=stream)
+            done += max(n, 2)
+            if info["residual"] < tol:
+                info["converged"] = True
+                break
+        return info
 
     def close(self):
         if self.handle:

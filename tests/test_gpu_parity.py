@@ -181,7 +181,9 @@ def test_adr_flux_plane_anywhere():
         assert np.allclose(info["flux"], want, rtol=1e-10, atol=1e-15)
 
 
-@pytest.mark.parametrize("prec,tol_eps,tol_c", [(lbm.LBM_F32, 1e-4, 1e-5),
+# concentration tolerance: float rounding (~6e-8 per operation) accumulated
+# over 1500 steps of a damped map stays near 1e-5; half storage 1e-2
+@pytest.mark.parametrize("prec,tol_eps,tol_c", [(lbm.LBM_F32, 1e-4, 1e-4),
                                                 (lbm.LBM_F16DEV, 1e-3, 1e-2)])
 def test_adr_reduced_precision(prec, tol_eps, tol_c):
     nx, ny, fib, k1, k2, solid, kab, kbc, ux, uy = _oracle_case("ragged")

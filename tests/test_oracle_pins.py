@@ -473,3 +473,74 @@ def test_steady_state_matches_dense_linear_solve():
     eps_exact = oracle.efficiency(prob.flux(gfull), ns)
     assert out["eps"] == pytest.approx(eps_exact, abs=1e-11)
     assert 0 < eps_exact < 1
+
+
+# ---------------------------------------------------------------------------
+# discrete adjoint of the oracle: pinned by central finite differences of
+# the oracle's own steady state (itself pinned to the dense solve above)
+# ---------------------------------------------------------------------------
+def _steady_eps(prob, steps):
+    return prob.run(steps)["eps"]
+
+
+@pytest.mark.parametrize("ns", [2, 3])
+def test_adjoint_rate_gradient_matches_finite_differences(ns):
+    """d eps / d k at every solid node from the adjoint equals the central
+    difference of the steady efficiency (h = 1e-5 relative)."""
+    solid, kab, kbc, ux, uy, tau, cin = _tiny_case(ns)
+    steps = 6000
+    prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, tau, cin)
+    fwd = prob.run(steps)
+    adj = oracle.adjoint(prob, fwd["g"], steps)
+    assert adj["eps"] == pytest.approx(fwd["eps"], abs=1e-15)
+    ys, xs = np.nonzero(solid)
+    checked = 0
+    for y, x in zip(ys, xs):
+        for field, grad in ((kab, adj["dkab"]), (kbc, adj["dkbc"])):
+            if ns < 3 and field is kbc:
+                continue
+            base = field[y, x] if field[y, x] > 0 else 0.1
+            h = 1e-5 * base
+            vals = []
+            for sgn in (1, -1):
+                f2 = field.copy()
+                f2[y, x] = field[y, x] + sgn * h
+                ka = f2 if field is kab else kab
+                kb = f2 if field is kbc else kbc
+                p2 = oracle.ADRProblem(solid, ka, kb, ux, uy, tau, cin)
+                vals.append(_steady_eps(p2, steps))
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert grad[y, x] == pytest.approx(fd, rel=1e-5, abs=1e-12)
+            checked += abs(fd) > 1e-8
+    assert checked >= 3
+
+
+def test_adjoint_fiber_weight_gradient_matches_finite_differences():
+    """Relaxed catalyst weights (k_AB = w k1, k_BC = (1-w) k2): d eps/d w_f
+    = sum over the fiber's nodes of k1 d eps/dk_AB - k2 d eps/dk_BC."""
+    nx, ny = 12, 7
+    k1, k2 = 0.2, 0.3
+    fib = np.array([[3.6, 3.1, 1.3, 1, 0, 0.7], [8.2, 3.8, 1.4, 1, 0, 0.25]])
+    rng = np.random.default_rng(3)
+    solid, kab, kbc = oracle.raster(nx, ny, fib, k1, k2)
+    ux = (0.05 + 0.01 * rng.random((ny, nx))) * (solid == 0)
+    uy = 0.01 * (rng.random((ny, nx)) - 0.5) * (solid == 0)
+    tau = [0.8, 0.75, 0.9]
+    steps = 6000
+    prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, tau, [1, 0, 0])
+    fwd = prob.run(steps)
+    adj = oracle.adjoint(prob, fwd["g"], steps)
+    ids = oracle.fiber_ids(nx, ny, fib)
+    dw = oracle.fiber_weight_gradient(ids, adj["dkab"], adj["dkbc"], k1, k2, 2)
+    h = 1e-5
+    for f in range(2):
+        vals = []
+        for sgn in (1, -1):
+            fb = fib.copy()
+            fb[f, 5] += sgn * h
+            s2, a2, b2 = oracle.raster(nx, ny, fb, k1, k2)
+            p2 = oracle.ADRProblem(s2, a2, b2, ux, uy, tau, [1, 0, 0])
+            vals.append(p2.run(steps)["eps"])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd) > 1e-6
+        assert dw[f] == pytest.approx(fd, rel=1e-5)
