@@ -28,7 +28,7 @@ namespace lbm {
 //   LBM_BLOCK_X        threads per block = nodes of one row segment
 //   LBM_ADR_MIN_BLOCKS resident blocks per SM asked of the register allocator
 #ifndef LBM_BLOCK_X
-#define LBM_BLOCK_X 128
+#define LBM_BLOCK_X 256
 #endif
 #ifndef LBM_ADR_MIN_BLOCKS
 #define LBM_ADR_MIN_BLOCKS 1

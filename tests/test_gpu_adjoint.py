@@ -137,3 +137,25 @@ def test_adjoint_f32_close_to_f64():
         out[prec] = dw.cpu().numpy()
     d64, d32 = out[lbm.LBM_F64], out[lbm.LBM_F32]
     assert np.abs(d32 - d64).max() <= 1e-3 * np.abs(d64).max()
+
+
+def test_autograd_function_matches_finite_differences():
+    """torch.autograd through MembraneProblem.efficiency: backward() runs the
+    adjoint; compare with central differences of the forward (h = 1e-4)."""
+    from paper_2109_04455_gb300.autograd import MembraneProblem
+    nx, ny, fib, k1, k2 = _geometry()
+    prob = MembraneProblem(nx, ny, fib, k1, k2, [0.7] * 3, tol=1e-13,
+                           check_every=500)
+    w = torch.tensor(fib[:, 5], dtype=torch.float64, requires_grad=True)
+    eps = prob.efficiency(w)
+    eps.backward()
+    g = w.grad.numpy()
+    h = 1e-4
+    for f in (0, fib.shape[0] - 1):
+        vals = []
+        for sgn in (1, -1):
+            w2 = w.detach().clone()
+            w2[f] += sgn * h
+            vals.append(float(prob.efficiency(w2)))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert g[f] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(g).max())
