@@ -83,14 +83,16 @@ __device__ __forceinline__ uint32_t nib(uint32_t word, int j) {
 }
 
 // ---------------------------------------------------------------------------
-// deterministic block reduction of K values: warp shuffles in the value type
-// A (float on the float paths, where double shuffles would cost more than the
-// lattice update on this part's narrow FP64 pipe), then the warp sums added
-// in double in a fixed order.  Result valid in thread 0.
+// deterministic block reduction of K values, stored by threads 0..K-1 (one
+// component each) to dst[0..K).  The block-level sums stay in the value type
+// A (float on the float paths): this part's FP64 pipe is narrow, and a chain
+// of double additions at the end of every block held each block's slot long
+// enough to multiply the time of a check step.  The grid-level sums of these
+// partials are taken in double by reduce_partials_kernel.
 // ---------------------------------------------------------------------------
 template <int K, typename A>
-__device__ __forceinline__ void block_sum(const A (&v)[K], double (&out)[K]) {
-  __shared__ double red[32][K];
+__device__ __forceinline__ void block_sum_store(const A (&v)[K], double *dst) {
+  __shared__ A red[32][K];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   A w[K];
 #pragma unroll
@@ -101,17 +103,14 @@ __device__ __forceinline__ void block_sum(const A (&v)[K], double (&out)[K]) {
   }
   if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) red[warp][k] = double(w[k]);
+    for (int k = 0; k < K; ++k) red[warp][k] = w[k];
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < K) {
     const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double s = 0.0;
-      for (int i = 0; i < nw; ++i) s += red[i][k];
-      out[k] = s;
-    }
+    A s = A(0);
+    for (int i = 0; i < nw; ++i) s += red[i][threadIdx.x];
+    dst[threadIdx.x] = double(s);
   }
 }
 
@@ -329,14 +328,9 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
   }
 
   if (MODE == kAdrCheck) {
-    double tot[2 * NS];
-    block_sum<2 * NS, T>(acc, tot);
-    if (threadIdx.x == 0) {
-      const long long b = LIST ? a.part_off + blockIdx.x
-                               : (long long)blockIdx.y * gridDim.x + blockIdx.x;
-#pragma unroll
-      for (int k = 0; k < 2 * NS; ++k) a.partials[b * (2 * NS) + k] = tot[k];
-    }
+    const long long b = LIST ? a.part_off + blockIdx.x
+                             : (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    block_sum_store<2 * NS, T>(acc, a.partials + b * (2 * NS));
   }
 }
 
@@ -378,6 +372,14 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
           g[s][i] = P::load(src[(long long)(s * 9 + i) * plane + n - (cy(i) * np + cx(i))]) +
                     adr_shift<P>(a, s, i);
       }
+      // the previous concentrations are loaded with the populations, so the
+      // check step waits on memory once, like the plain step
+      T *__restrict__ cp = static_cast<T *>(a.cprev);
+      T prev[NS];
+      if (MODE == kAdrCheck) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) prev[s] = cp[s * plane + n];
+      }
       T E[9];
       eq_factors<T>(U[n], U[plane + n], E);
 #pragma unroll
@@ -391,8 +393,7 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
           dst[(long long)(s * 9 + i) * plane + n] =
               P::store(g[s][i] + om * (c * E[i] - g[s][i]) - adr_shift<P>(a, s, i));
         if (MODE == kAdrCheck) {
-          T *cp = static_cast<T *>(a.cprev);
-          acc[2 * s] = absT(c - cp[s * plane + n]);
+          acc[2 * s] = absT(c - prev[s]);
           acc[2 * s + 1] = absT(c);
           cp[s * plane + n] = c;
         }
@@ -442,6 +443,15 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
         g1[s][i] = P::load(hi) + sh;
       }
     }
+    T *__restrict__ cpb = static_cast<T *>(a.cprev) + n0;
+    T prev0[NS], prev1[NS];
+    if (MODE == kAdrCheck && valid) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        prev0[s] = cpb[s * plane];
+        prev1[s] = cpb[s * plane + 1];
+      }
+    }
     if (valid && (in0 || in1)) {
       const VT ux = *reinterpret_cast<const VT *>(U + n0);
       const VT uy = *reinterpret_cast<const VT *>(U + plane + n0);
@@ -477,16 +487,15 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
           }
         }
         if (MODE == kAdrCheck) {
-          T *cp = static_cast<T *>(a.cprev) + s * plane + n0;
           if (in0) {
-            acc[2 * s] += absT(c0 - cp[0]);
+            acc[2 * s] += absT(c0 - prev0[s]);
             acc[2 * s + 1] += absT(c0);
-            cp[0] = c0;
+            cpb[s * plane] = c0;
           }
           if (in1) {
-            acc[2 * s] += absT(c1 - cp[1]);
+            acc[2 * s] += absT(c1 - prev1[s]);
             acc[2 * s + 1] += absT(c1);
-            cp[1] = c1;
+            cpb[s * plane + 1] = c1;
           }
         }
       }
@@ -494,13 +503,8 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
   }
 
   if (MODE == kAdrCheck) {
-    double tot[2 * NS];
-    block_sum<2 * NS, T>(acc, tot);
-    if (threadIdx.x == 0) {
-      const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-#pragma unroll
-      for (int k = 0; k < 2 * NS; ++k) a.partials[b * (2 * NS) + k] = tot[k];
-    }
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    block_sum_store<2 * NS, T>(acc, a.partials + b * (2 * NS));
   }
 }
 
@@ -533,12 +537,9 @@ __global__ void __launch_bounds__(kReduceThreads)
       acc[s] += v;
     }
   }
-  double tot[NS];
-  block_sum<NS, double>(acc, tot);
-  if (threadIdx.x == 0) {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) out[s] = tot[s] / double(ny);
-  }
+  for (int s = 0; s < NS; ++s) acc[s] /= double(ny);
+  block_sum_store<NS, double>(acc, out);
 }
 
 // Sum rows of K partials in a fixed order.  Block b of the grid adds the
@@ -558,12 +559,7 @@ __global__ void __launch_bounds__(kReduceThreads)
 #pragma unroll
     for (int k = 0; k < K; ++k) acc[k] += partials[b * K + k];
   }
-  double tot[K];
-  block_sum<K, double>(acc, tot);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) out[(long long)blockIdx.x * K + k] = tot[k];
-  }
+  block_sum_store<K, double>(acc, out + (long long)blockIdx.x * K);
 }
 
 // ---------------------------------------------------------------------------
@@ -689,13 +685,8 @@ __global__ void __launch_bounds__(kBlockX) adj_kernel(const AdjArgs a) {
     }
   }
   if (MODE == kAdjCheck) {
-    double tot[2];
-    block_sum<2, T>(acc, tot);
-    if (threadIdx.x == 0) {
-      const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-      a.partials[b * 2] = tot[0];
-      a.partials[b * 2 + 1] = tot[1];
-    }
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    block_sum_store<2, T>(acc, a.partials + b * 2);
   }
 }
 
@@ -864,13 +855,8 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
   }
 
   if (MODE == kFlowCheck) {
-    double tot[2];
-    block_sum<2, T>(acc, tot);
-    if (threadIdx.x == 0) {
-      const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-      a.partials[b * 2] = tot[0];
-      a.partials[b * 2 + 1] = tot[1];
-    }
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    block_sum_store<2, T>(acc, a.partials + b * 2);
   }
 }
 

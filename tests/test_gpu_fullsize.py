@@ -1,0 +1,81 @@
+"""Checks on the full benchmark lattice (16384 x 4096, 2000 fibers), in the
+launch configuration bench.py times.  The oracle cannot run this size, so
+these are properties that hold at any size:
+* FP32 and FP16-deviation storage against an FP64 GPU run of the same size
+  (efficiency within 1e-4 and 1e-3);
+* the species-sum invariant (A+B+C of the cascade equals one non-reacting
+  species when every species has the anti-bounce-back inlet and the same
+  tau, because the sources on each link add to zero);
+* no catalyst, no product: B and C stay exactly zero."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2109_04455_gb300 import inputs, lbm  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+PLANE = 3700        # just downstream of the first (A->B) membrane
+STEPS = 2000
+
+
+@pytest.fixture(scope="module")
+def big():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_04455_gb300 import _build
+    _build.build()
+    w = inputs.large_membrane()
+    geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
+    u64, _ = lbm.lbm_flow_solve(geom, w.tau_flow, w.u0, 500,
+                                precision=lbm.LBM_F64)
+    return w, geom, u64
+
+
+def _eps_ab(flux):
+    return flux[1] / (flux[0] + flux[1])
+
+
+def test_full_size_reduced_precision_against_f64(big):
+    w, geom, u64 = big
+    out = {}
+    for prec in (lbm.LBM_F64, lbm.LBM_F32, lbm.LBM_F16DEV):
+        u = u64 if prec == lbm.LBM_F64 else u64.float()
+        prm = lbm.adr_params(3, w.tau_c, precision=prec, max_steps=STEPS,
+                             x_plane=PLANE)
+        _, info = lbm.lbm_adr_solve(geom, prm, u, want_conc=False)
+        out[prec] = info
+        torch.cuda.empty_cache()
+    e64 = _eps_ab(out[lbm.LBM_F64]["flux"])
+    assert e64 > 1e-3
+    assert abs(_eps_ab(out[lbm.LBM_F32]["flux"]) - e64) < 1e-4
+    assert abs(_eps_ab(out[lbm.LBM_F16DEV]["flux"]) - e64) < 1e-3
+    for prec in (lbm.LBM_F32, lbm.LBM_F16DEV):
+        assert abs(out[prec]["eps"] - out[lbm.LBM_F64]["eps"]) < 1e-3
+
+
+def test_full_size_species_sum_invariant(big):
+    w, geom, u64 = big
+    u = u64.float()
+    flags = lbm.LBM_ADR_INLET_ABB_ALL
+    prm3 = lbm.adr_params(3, w.tau_c, precision=lbm.LBM_F32, max_steps=300,
+                          flags=flags)
+    c3, _ = lbm.lbm_adr_solve(geom, prm3, u)
+    total = c3.sum(dim=0)
+    del c3
+    g0 = lbm.Geometry(w.nx, w.ny, w.fibers, 0.0, 0.0).upload()
+    prm1 = lbm.adr_params(1, w.tau_c, precision=lbm.LBM_F32, max_steps=300,
+                          flags=flags)
+    c1, _ = lbm.lbm_adr_solve(g0, prm1, u)
+    diff = (total - c1[0]).abs().max().item()
+    assert diff < 2e-5          # float rounding of O(1) concentrations
+
+
+def test_full_size_no_catalyst_no_product(big):
+    w, geom, u64 = big
+    g0 = lbm.Geometry(w.nx, w.ny, w.fibers, 0.0, 0.0).upload()
+    prm = lbm.adr_params(3, w.tau_c, precision=lbm.LBM_F32, max_steps=200)
+    c, info = lbm.lbm_adr_solve(g0, prm, u64.float())
+    assert torch.count_nonzero(c[1:]).item() == 0
+    assert info["flux"][1] == 0.0 and info["flux"][2] == 0.0
