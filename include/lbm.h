@@ -232,6 +232,25 @@ lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps, double tol,
  * Host arithmetic only.  LBM_EINVAL for other nspecies or a zero sum. */
 lbm_status lbm_efficiency(const double *flux, int32_t nspecies, double *eps);
 
+/* Outfluxes N_s on the plane x_plane (< 0 selects nx - 3) of the solver's
+ * current state, written to flux_out (host, 3 doubles; 0 for absent
+ * species), without any device workspace.  The paper has no counterpart:
+ * this serves callers that cannot allocate device memory where they need
+ * the fluxes, such as a monitor or plugin inside an application whose own
+ * memory pool has reserved the whole GPU (a cudaMalloc would fail or
+ * fragment it), or a time-critical loop that must not pay cudaMalloc's
+ * implicit device synchronisation.  Its partial sums live in a fixed 6 KB
+ * device array that every GPU loading this library holds until the process
+ * exits; it covers at most 65536 lattice rows, and a larger ny is rejected
+ * with LBM_EINVAL.  The first call on a device looks up that array's device
+ * address, so make the first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's values (each call
+ * rewrites every slot it reads, so nothing needs clearing); calls whose GPU
+ * work overlaps (other streams or threads) race on it and must be
+ * serialised by the caller.  Synchronises `stream`. */
+lbm_status lbm_adr_outflux_noalloc(lbm_adr_solver *s, int32_t x_plane,
+                                   void *stream, double *flux_out);
+
 #ifdef __cplusplus
 }
 #endif

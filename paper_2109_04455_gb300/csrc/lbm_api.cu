@@ -3,6 +3,7 @@
 // is the caller's; this file only launches kernels on the caller's stream.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -807,4 +808,178 @@ extern "C" lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps,
     if (lbm_efficiency(flux, ns, &eps) == LBM_OK) info->eps = eps;
   }
   return stt;
+}
+
+// ---------------------------------------------------------------------------
+// outflux without any workspace
+//
+// For callers that cannot allocate device memory at the point where they
+// want the fluxes: e.g. a monitor or plugin running inside an application
+// that reserved all device memory for its own pool at start-up (a cudaMalloc
+// would fail or fragment that pool), or a time-critical loop that must not
+// pay cudaMalloc's implicit device synchronisation.  Instead of a caller
+// workspace, the per-block partial sums live in the fixed-size array below,
+// which every GPU that loads this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace lbm {
+namespace noalloc {
+constexpr int kRowsPerBlock = 256;
+constexpr int kMaxRows = 65536;  // a geometry has at most 65535 rows
+constexpr int kMaxBlocks = kMaxRows / kRowsPerBlock;
+constexpr int kFinal = kMaxBlocks * 3;  // offset of the result
+}  // namespace noalloc
+}  // namespace lbm
+
+// [kMaxBlocks][3] block partial sums, then the 3 outfluxes (6 KB per GPU)
+static __device__ __align__(256) double
+    g_noalloc_scratch[lbm::noalloc::kMaxBlocks * 3 + 3];
+
+namespace lbm {
+namespace noalloc {
+
+static std::mutex g_mutex;
+static double *g_addr[256] = {};  // device address of the array, per device
+
+// Rows [b*256, b*256+256) of the plane x = xp: per species the sum over those
+// rows of sum_i c_ix g*_{s,i}, written to part[b*3 + s].  Every block writes
+// all three slots, so nothing has to start at zero.
+template <class P, int NS>
+__global__ void __launch_bounds__(kRowsPerBlock)
+    outflux_partial_noalloc_kernel(const void *g, const uint32_t *links,
+                                   long long plane, int nx_pad, int ny, int xp,
+                                   double cref0, double cref1, double cref2,
+                                   double *part) {
+  using S = typename P::S;
+  const S *src = static_cast<const S *>(g);
+  const double cref[3] = {cref0, cref1, cref2};
+  const int y = blockIdx.x * kRowsPerBlock + threadIdx.x;
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (y < ny) {
+    const long long n = (long long)y * nx_pad + xp;
+    if (links[n] != kSolidNode) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+          if (cx(i) == 0) continue;
+          double gi = double(P::load(src[(long long)(s * 9 + i) * plane + n]));
+          if (P::kDev) gi += double(Lattice<float>::w(i)) * cref[s];
+          acc[s] += cx(i) > 0 ? gi : -gi;
+        }
+      }
+    }
+  }
+  block_sum_store<3, double>(acc, part + blockIdx.x * 3);
+}
+
+// One block: out[s] = (sum over the nb block partials) / ny.
+__global__ void __launch_bounds__(kReduceThreads)
+    outflux_final_noalloc_kernel(const double *part, int nb, int ny,
+                                 double *out) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+#pragma unroll
+    for (int s = 0; s < 3; ++s) acc[s] += part[b * 3 + s];
+  }
+#pragma unroll
+  for (int s = 0; s < 3; ++s) acc[s] /= double(ny);
+  block_sum_store<3, double>(acc, out);
+}
+
+template <class P>
+cudaError_t outflux_noalloc_launch(int ns, const void *g, const uint32_t *links,
+                                   long long plane, int nx_pad, int ny, int xp,
+                                   const double *cref, double *scratch,
+                                   cudaStream_t st) {
+  const int nb = (ny + kRowsPerBlock - 1) / kRowsPerBlock;
+  const dim3 block(kRowsPerBlock);
+  switch (ns) {
+    case 1:
+      outflux_partial_noalloc_kernel<P, 1><<<nb, block, 0, st>>>(
+          g, links, plane, nx_pad, ny, xp, cref[0], cref[1], cref[2], scratch);
+      break;
+    case 2:
+      outflux_partial_noalloc_kernel<P, 2><<<nb, block, 0, st>>>(
+          g, links, plane, nx_pad, ny, xp, cref[0], cref[1], cref[2], scratch);
+      break;
+    default:
+      outflux_partial_noalloc_kernel<P, 3><<<nb, block, 0, st>>>(
+          g, links, plane, nx_pad, ny, xp, cref[0], cref[1], cref[2], scratch);
+      break;
+  }
+  outflux_final_noalloc_kernel<<<1, dim3(kReduceThreads), 0, st>>>(
+      scratch, nb, ny, scratch + kFinal);
+  return cudaGetLastError();
+}
+
+}  // namespace noalloc
+}  // namespace lbm
+
+extern "C" lbm_status lbm_adr_outflux_noalloc(lbm_adr_solver *s,
+                                              int32_t x_plane, void *stream,
+                                              double *flux_out) {
+  if (!s || !flux_out) {
+    set_error("lbm_adr_outflux_noalloc: NULL argument");
+    return LBM_EINVAL;
+  }
+  const lbm_geometry *g = s->g;
+  const int xp = x_plane < 0 ? g->nx - 3 : x_plane;
+  if (xp >= g->nx) {
+    set_error("lbm_adr_outflux_noalloc: flux plane outside the lattice");
+    return LBM_EINVAL;
+  }
+  if (g->ny > noalloc::kMaxRows) {
+    set_error("lbm_adr_outflux_noalloc: ny = " + std::to_string(g->ny) +
+              " exceeds the " + std::to_string(noalloc::kMaxRows) +
+              "-row limit of its fixed scratch array");
+    return LBM_EINVAL;
+  }
+  if (lbm_status bs = bind_device(s->buf[0], "lbm_adr_outflux_noalloc")) return bs;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_outflux_noalloc", e);
+  if (dev < 0 || dev >= 256) {
+    set_error("lbm_adr_outflux_noalloc: device index out of range");
+    return LBM_EINVAL;
+  }
+  double *scratch = nullptr;
+  {
+    // first call on a device: look up the array's device address once
+    std::lock_guard<std::mutex> lock(noalloc::g_mutex);
+    if (!noalloc::g_addr[dev]) {
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail("lbm_adr_outflux_noalloc(setup)", e);
+      noalloc::g_addr[dev] = static_cast<double *>(p);
+    }
+    scratch = noalloc::g_addr[dev];
+  }
+  cudaStream_t st = as_stream(stream);
+  const void *cur = s->buf[s->cur];
+  const int ns = s->p.nspecies;
+  switch (s->p.precision) {
+    case LBM_F64:
+      e = noalloc::outflux_noalloc_launch<PrecF64>(ns, cur, g->d_links, plane_of(g),
+                                          g->nx_pad, g->ny, xp, s->a.cref,
+                                          scratch, st);
+      break;
+    case LBM_F32:
+      e = noalloc::outflux_noalloc_launch<PrecF32>(ns, cur, g->d_links, plane_of(g),
+                                          g->nx_pad, g->ny, xp, s->a.cref,
+                                          scratch, st);
+      break;
+    default:
+      e = noalloc::outflux_noalloc_launch<PrecF16Dev>(ns, cur, g->d_links, plane_of(g),
+                                             g->nx_pad, g->ny, xp, s->a.cref,
+                                             scratch, st);
+      break;
+  }
+  double h[3] = {0.0, 0.0, 0.0};
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h, scratch + noalloc::kFinal, sizeof(h),
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_outflux_noalloc", e);
+  for (int k = 0; k < 3; ++k) flux_out[k] = k < ns ? h[k] : 0.0;
+  return LBM_OK;
 }

@@ -84,6 +84,7 @@ _SIGS = {
     "lbm_adr_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_size_t, _P, _P,
                                      _P]),
     "lbm_efficiency": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "lbm_adr_outflux_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "lbm_adr_adjoint_ws_bytes": (ctypes.c_size_t, [_P, _P]),
     "lbm_adr_adjoint": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double,
                                        ctypes.c_int32, _P, ctypes.c_size_t,
@@ -336,6 +337,17 @@ class ADRSolver:
             pass
 
 
+def lbm_adr_outflux_noalloc(solver: "ADRSolver", x_plane: int = -1,
+                            stream=None):
+    """Outfluxes N_A, N_B, N_C of the solver's current state on a plane,
+    computed without any device allocation (for callers that cannot
+    allocate; see include/lbm.h for the shared fixed scratch it uses)."""
+    out = (ctypes.c_double * 3)()
+    _check(load().lbm_adr_outflux_noalloc(solver.handle, int(x_plane),
+                                          _stream_ptr(stream), out))
+    return [float(v) for v in out]
+
+
 def lbm_adr_solve(geom: Geometry, params: lbm_adr_params, u, stream=None,
                   want_conc: bool = True,
                   raise_not_converged: bool = False):
@@ -359,3 +371,4 @@ def lbm_adr_solve(geom: Geometry, params: lbm_adr_params, u, stream=None,
                              not raise_not_converged):
         _check(st)
     return conc, info.as_dict()
+
