@@ -228,6 +228,52 @@ lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps, double tol,
                            void *dkab, void *dkbc, void *dw, void *stream,
                            lbm_solve_info *info);
 
+/* ------------------------------------------------------------------------ */
+/* Batched ADR solves (a Pe x Da sweep over many lattices of uneven size).  */
+/* Every active lattice advances in the same persistent launch per time     */
+/* step (interior row tiles and boundary-node chunks of all lattices in one */
+/* work list); a check interval (check_every steps, the last two recording  */
+/* the residual, then the per-lattice sums and outfluxes) is captured once  */
+/* as a CUDA graph and replayed; a lattice leaves the work list once its    */
+/* residual is below its tol or it reached its max_steps.  The per-node     */
+/* arithmetic is that of lbm_adr_solve, so each lattice's result equals its */
+/* unbatched solve.  The launch shape (tile width 128 or 256, persistent    */
+/* grid size) is chosen by timing the candidates on the batch.              */
+/* ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch;
+
+/* Device bytes for `count` lattices (all with the same nspecies, 2 or 3, and
+ * the same precision); 0 if the arguments are invalid. */
+size_t lbm_batch_ws_bytes(int32_t count, const lbm_geometry *const *geoms,
+                          const lbm_adr_params *params);
+
+/* geoms[i] uploaded, params[i] its ADR settings (tol, max_steps and x_plane
+ * per lattice; check_every of params[0] for all, rounded up to even; a
+ * lattice runs whole check intervals, so max_steps is rounded up to a
+ * multiple of it; tol <= 0 runs exactly that many steps),
+ * u[i] its device velocity.  ws holds every lattice's populations. */
+lbm_status lbm_batch_create(int32_t count, const lbm_geometry *const *geoms,
+                            const lbm_adr_params *params,
+                            const void *const *u, void *ws, size_t ws_bytes,
+                            lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *b);
+
+/* Time the launch-shape candidates on this batch and keep the fastest
+ * (tile width in *tile, blocks in *grid; either may be NULL).  Runs by
+ * itself on the first lbm_batch_solve. */
+lbm_status lbm_batch_tune(lbm_batch *b, void *stream, int32_t *tile,
+                          int32_t *grid);
+
+/* The chosen launch shape and the measured ms per step of the candidates
+ * (tile 128 then 256, grids 1, 2, 4, 8 x resident blocks; 8 floats). */
+lbm_status lbm_batch_tuning(const lbm_batch *b, int32_t *tile, int32_t *grid,
+                            float *ms_per_step);
+
+/* Solve every lattice from its initial state; infos[count] receives steps,
+ * residual, converged, outfluxes and efficiency per lattice.
+ * LBM_ENOTCONVERGED if any lattice stopped at max_steps. */
+lbm_status lbm_batch_solve(lbm_batch *b, void *stream, lbm_solve_info *infos);
+
 /* Eq. (A-B): eps = N_B/(N_A+N_B) for nspecies 2, N_C/(N_A+N_B+N_C) for 3.
  * Host arithmetic only.  LBM_EINVAL for other nspecies or a zero sum. */
 lbm_status lbm_efficiency(const double *flux, int32_t nspecies, double *eps);

@@ -69,6 +69,10 @@ size_t store_bytes(int prec) {
   return prec == LBM_F64 ? 8 : (prec == LBM_F32 ? 4 : 2);
 }
 size_t compute_bytes(int prec) { return prec == LBM_F64 ? 8 : 4; }
+int prec_vec(int prec) {
+  return prec == LBM_F64 ? PrecF64::kVec
+                         : (prec == LBM_F32 ? PrecF32::kVec : PrecF16Dev::kVec);
+}
 
 // Make the device that owns `p` current for this thread (the caller's
 // buffers decide where the work runs); rejects host memory.
@@ -309,6 +313,7 @@ struct lbm_adr_solver {
   int64_t steps = 0;
   bool has_check = false;
   long long nb = 0;
+  AdrOverlap ov;   // boundary kernel beside the bulk kernel
 };
 
 struct AdrLayout {
@@ -322,7 +327,8 @@ static AdrLayout adr_layout(const lbm_geometry *g, const lbm_adr_params *p) {
   l.buf = align256(ns * 9 * pl * store_bytes(p->precision));
   l.cprev = align256(ns * pl * compute_bytes(p->precision));
   l.partials = align256(static_cast<size_t>(adr_partial_rows(
-                            g->nx_pad, g->ny, static_cast<long long>(g->bnodes.size()))) *
+                            prec_vec(p->precision), g->nx_pad, g->ny,
+                            static_cast<long long>(g->bnodes.size()))) *
                         2 * ns * 8);
   l.scratch = align256(kReduceGrid * 2 * ns * 8);
   l.result = align256(64 * 8);
@@ -345,11 +351,11 @@ extern "C" size_t lbm_adr_ws_bytes(const lbm_geometry *g,
 }
 
 static cudaError_t adr_launch(int prec, int ns, int mode, const AdrArgs &a,
-                              cudaStream_t st) {
+                              cudaStream_t st, const AdrOverlap *ov = nullptr) {
   switch (prec) {
-    case LBM_F64: return launch_adr<PrecF64>(ns, mode, a, st);
-    case LBM_F32: return launch_adr<PrecF32>(ns, mode, a, st);
-    default: return launch_adr<PrecF16Dev>(ns, mode, a, st);
+    case LBM_F64: return launch_adr<PrecF64>(ns, mode, a, st, ov);
+    case LBM_F32: return launch_adr<PrecF32>(ns, mode, a, st, ov);
+    default: return launch_adr<PrecF16Dev>(ns, mode, a, st, ov);
   }
 }
 
@@ -424,7 +430,8 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
   s->scratch = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials);
   s->result = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials +
                                          l.scratch);
-  s->nb = adr_partial_rows(g->nx_pad, g->ny, static_cast<long long>(g->bnodes.size()));
+  s->nb = adr_partial_rows(prec_vec(p->precision), g->nx_pad, g->ny,
+                           static_cast<long long>(g->bnodes.size()));
   AdrArgs &a = s->a;
   a.links = g->d_links;
   a.kab = g->d_kab;
@@ -449,11 +456,29 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
     a.fcin[k] = static_cast<float>(a.cin[k]);
     a.fcref[k] = static_cast<float>(a.cref[k]);
   }
+  // second stream for the boundary-node kernel (no device memory involved)
+  if (!g->bnodes.empty()) {
+    cudaError_t e = cudaStreamCreateWithFlags(&s->ov.aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+      e = cudaEventCreateWithFlags(&s->ov.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+      e = cudaEventCreateWithFlags(&s->ov.join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      lbm_adr_destroy(s);
+      return cuda_fail("lbm_adr_create", e);
+    }
+  }
   *out = s;
   return LBM_OK;
 }
 
-extern "C" void lbm_adr_destroy(lbm_adr_solver *s) { delete s; }
+extern "C" void lbm_adr_destroy(lbm_adr_solver *s) {
+  if (!s) return;
+  if (s->ov.fork) cudaEventDestroy(s->ov.fork);
+  if (s->ov.join) cudaEventDestroy(s->ov.join);
+  if (s->ov.aux) cudaStreamDestroy(s->ov.aux);
+  delete s;
+}
 
 extern "C" lbm_status lbm_adr_init(lbm_adr_solver *s, void *stream) {
   if (!s) {
@@ -482,7 +507,7 @@ static cudaError_t adr_step(lbm_adr_solver *s, int mode, cudaStream_t st) {
   a.dst = s->buf[s->cur ^ 1];
   s->cur ^= 1;
   ++s->steps;
-  return adr_launch(s->p.precision, s->p.nspecies, mode, a, st);
+  return adr_launch(s->p.precision, s->p.nspecies, mode, a, st, &s->ov);
 }
 
 extern "C" lbm_status lbm_adr_run(lbm_adr_solver *s, int64_t nsteps,

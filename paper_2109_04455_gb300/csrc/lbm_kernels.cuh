@@ -39,10 +39,16 @@ constexpr int kReduceThreads = 256;
 // ---------------------------------------------------------------------------
 // precision traits: storage type S, compute type T
 // ---------------------------------------------------------------------------
+// nodes per thread of the bulk step (LBM_ADR_VEC_F16 overrides the half
+// path's choice; two nodes keep twice the bytes of 2-byte loads in flight)
+#ifndef LBM_ADR_VEC_F16
+#define LBM_ADR_VEC_F16 2
+#endif
 struct PrecF64 {
   using S = double;
   using T = double;
   static constexpr bool kDev = false;
+  static constexpr int kVec = 1;
   static __device__ __forceinline__ T load(S v) { return v; }
   static __device__ __forceinline__ S store(T v) { return v; }
 };
@@ -50,6 +56,7 @@ struct PrecF32 {
   using S = float;
   using T = float;
   static constexpr bool kDev = false;
+  static constexpr int kVec = 1;
   static __device__ __forceinline__ T load(S v) { return v; }
   static __device__ __forceinline__ S store(T v) { return v; }
 };
@@ -58,6 +65,7 @@ struct PrecF16Dev {
   using S = __half;
   using T = float;
   static constexpr bool kDev = true;
+  static constexpr int kVec = LBM_ADR_VEC_F16;
   static __device__ __forceinline__ T load(S v) { return __half2float(v); }
   static __device__ __forceinline__ S store(T v) { return __float2half_rn(v); }
 };
@@ -125,6 +133,10 @@ __device__ __forceinline__ S zero_of() { return S(0); }
 template <>
 __device__ __forceinline__ __half zero_of<__half>() { return __float2half_rn(0.0f); }
 
+__device__ __forceinline__ double2 pack2(double lo, double hi) { return make_double2(lo, hi); }
+__device__ __forceinline__ float2 pack2(float lo, float hi) { return make_float2(lo, hi); }
+__device__ __forceinline__ __half2 pack2(__half lo, __half hi) { return __halves2half2(lo, hi); }
+
 // Kernel parameters come in double and in float; the float paths read the
 // float copy, so no thread converts a double (this part's FP64 pipe is
 // narrow enough for per-thread conversions to show up in a step's time).
@@ -155,6 +167,7 @@ struct AdrArgs {
   long long plane;          // ny * nx_pad
   int nx, ny, nx_pad;
   int abb_all;              // anti-bounce-back inlet for every species
+  int xp;                   // flux plane
   double omega[3];          // 1/tau per species
   double cin[3];            // inlet concentration per species
   double cref[3];           // reference concentration of the stored deviation
@@ -263,15 +276,106 @@ __device__ __forceinline__ typename P::T adr_collide(const AdrArgs &a, int s,
   return c;
 }
 
+// Update of one fluid node x = n % nx_pad with every link rule in place (or
+// its initial state): the species one after the other.
+template <class P, int NS, int MODE>
+__device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
+                                                 int x, uint32_t lw,
+                                                 typename P::T (&acc)[2 * NS]) {
+  using S = typename P::S;
+  using T = typename P::T;
+  const long long plane = a.plane;
+  S *__restrict__ dst = static_cast<S *>(a.dst);
+  const T *__restrict__ U = static_cast<const T *>(a.u);
+  const long long np = (long long)a.nx_pad;
+  T E[9];
+  eq_factors<T>(U[n], U[plane + n], E);
+  T C[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    T g[9];
+    if (MODE == kAdrInit) {
+      const T c0 = (s == 0) ? T(1) : T(0);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) g[i] = c0 * E[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        // pull from x - c_i when that node is fluid (always for lw == 0)
+        if (i == 0 || lw == 0u || nib(lw, opp(i)) == kFluid)
+          g[i] = adr_ld<P>(a, s, i, n - (cy(i) * np + cx(i)));
+      }
+      if (lw != 0u) adr_boundary<P>(a, s, lw, n, x, g);
+    }
+    const T c = adr_collide<P, NS>(a, s, lw, n, E, g, C);
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      dst[(long long)(s * 9 + i) * plane + n] = P::store(g[i] - adr_shift<P>(a, s, i));
+    if (MODE == kAdrCheck) {
+      T *cp = static_cast<T *>(a.cprev);
+      acc[2 * s] += absT(c - cp[s * plane + n]);
+      acc[2 * s + 1] += absT(c);
+      cp[s * plane + n] = c;
+    }
+  }
+}
+
+// Update of one interior node (link word 0: every neighbour is fluid): the
+// interior formula (pull from x - c_i, BGK, no source).  All populations of
+// all species are loaded before any arithmetic, so a thread keeps NS*9
+// independent loads in flight.
+template <class P, int NS, int MODE>
+__device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
+                                                  typename P::T (&acc)[2 * NS]) {
+  using S = typename P::S;
+  using T = typename P::T;
+  const long long np = a.nx_pad, plane = a.plane;
+  const S *__restrict__ src = static_cast<const S *>(a.src);
+  S *__restrict__ dst = static_cast<S *>(a.dst);
+  const T *__restrict__ U = static_cast<const T *>(a.u);
+  T g[NS][9];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      g[s][i] = P::load(src[(long long)(s * 9 + i) * plane + n - (cy(i) * np + cx(i))]) +
+                adr_shift<P>(a, s, i);
+  }
+  // the previous concentrations are loaded with the populations, so the
+  // check step waits on memory once, like the plain step
+  T *__restrict__ cp = static_cast<T *>(a.cprev);
+  T prev[NS];
+  if (MODE == kAdrCheck) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) prev[s] = cp[s * plane + n];
+  }
+  T E[9];
+  eq_factors<T>(U[n], U[plane + n], E);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    T c = T(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) c += g[s][i];
+    const T om = pick<T>(a.omega[s], a.fomega[s]);
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      dst[(long long)(s * 9 + i) * plane + n] =
+          P::store(g[s][i] + om * (c * E[i] - g[s][i]) - adr_shift<P>(a, s, i));
+    if (MODE == kAdrCheck) {
+      acc[2 * s] += absT(c - prev[s]);
+      acc[2 * s + 1] += absT(c);
+      cp[s * plane + n] = c;
+    }
+  }
+}
+
 // One node per thread, every link rule handled in place.  LIST = false: the
 // whole lattice (initial state; also the plain one-kernel step).  LIST = true:
 // only the boundary nodes of a.bnodes, after the bulk kernel (below) has
-// written the interior formula everywhere; its partial sums go to rows
-// a.part_off + block.
+// updated the interior nodes; its partial sums go to rows a.part_off + block.
 template <class P, int NS, int MODE, bool LIST>
 __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
     adr_node_kernel(const AdrArgs a) {
-  using S = typename P::S;
   using T = typename P::T;
   long long n;
   int x;
@@ -286,47 +390,10 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
     n = (long long)blockIdx.y * a.nx_pad + x;
     lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
   }
-  const long long plane = a.plane;
   T acc[2 * NS];
 #pragma unroll
   for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
-
-  if (lw != kSolidNode) {
-    S *__restrict__ dst = static_cast<S *>(a.dst);
-    const T *__restrict__ U = static_cast<const T *>(a.u);
-    const long long np = (long long)a.nx_pad;
-    T E[9];
-    eq_factors<T>(U[n], U[plane + n], E);
-    T C[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      T g[9];
-      if (MODE == kAdrInit) {
-        const T c0 = (s == 0) ? T(1) : T(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) g[i] = c0 * E[i];
-      } else {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          // pull from x - c_i when that node is fluid (always for lw == 0)
-          if (i == 0 || lw == 0u || nib(lw, opp(i)) == kFluid)
-            g[i] = adr_ld<P>(a, s, i, n - (cy(i) * np + cx(i)));
-        }
-        if (lw != 0u) adr_boundary<P>(a, s, lw, n, x, g);
-      }
-      const T c = adr_collide<P, NS>(a, s, lw, n, E, g, C);
-#pragma unroll
-      for (int i = 0; i < 9; ++i)
-        dst[(long long)(s * 9 + i) * plane + n] = P::store(g[i] - adr_shift<P>(a, s, i));
-      if (MODE == kAdrCheck) {
-        T *cp = static_cast<T *>(a.cprev);
-        acc[2 * s] = absT(c - cp[s * plane + n]);
-        acc[2 * s + 1] = absT(c);
-        cp[s * plane + n] = c;
-      }
-    }
-  }
-
+  if (lw != kSolidNode) adr_general_node<P, NS, MODE>(a, n, x, lw, acc);
   if (MODE == kAdrCheck) {
     const long long b = LIST ? a.part_off + blockIdx.x
                              : (long long)blockIdx.y * gridDim.x + blockIdx.x;
@@ -334,11 +401,9 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
   }
 }
 
-// Bulk step: the interior formula (pull from x - c_i, BGK, no source) for
-// the nodes whose eight neighbours are all fluid (link word 0); every other
-// node is left to adr_node_kernel<..., LIST = true>, launched right after.
-// All populations of all species are loaded before any arithmetic, so a
-// thread keeps NS*9 independent loads in flight.  VEC = 2 gives each thread
+// Bulk step: the interior formula for the nodes whose eight neighbours are
+// all fluid (link word 0); every other node is left to
+// adr_node_kernel<..., LIST = true>, launched right after.  VEC = 2 gives each thread
 // two nodes (x0 = 2t, x0 + 1): every plane is read with aligned two-wide
 // vector loads, the element a horizontal or diagonal pull needs from the
 // next pair over (x0 - 1 or x0 + 2) comes from the adjacent lane by a warp
@@ -363,42 +428,7 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
     const int x = blockIdx.x * kBlockX + threadIdx.x;
     const long long n = (long long)y * np + x;
     const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
-    if (lw == 0u) {
-      T g[NS][9];
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-          g[s][i] = P::load(src[(long long)(s * 9 + i) * plane + n - (cy(i) * np + cx(i))]) +
-                    adr_shift<P>(a, s, i);
-      }
-      // the previous concentrations are loaded with the populations, so the
-      // check step waits on memory once, like the plain step
-      T *__restrict__ cp = static_cast<T *>(a.cprev);
-      T prev[NS];
-      if (MODE == kAdrCheck) {
-#pragma unroll
-        for (int s = 0; s < NS; ++s) prev[s] = cp[s * plane + n];
-      }
-      T E[9];
-      eq_factors<T>(U[n], U[plane + n], E);
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        T c = T(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) c += g[s][i];
-        const T om = pick<T>(a.omega[s], a.fomega[s]);
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-          dst[(long long)(s * 9 + i) * plane + n] =
-              P::store(g[s][i] + om * (c * E[i] - g[s][i]) - adr_shift<P>(a, s, i));
-        if (MODE == kAdrCheck) {
-          acc[2 * s] = absT(c - prev[s]);
-          acc[2 * s + 1] = absT(c);
-          cp[s * plane + n] = c;
-        }
-      }
-    }
+    if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc);
   } else {
     using VS = typename Vec2<S>::type;
     using VT = typename Vec2<T>::type;
@@ -409,7 +439,9 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
     uint2 lw = make_uint2(kSolidNode, kSolidNode);
     if (valid) lw = *reinterpret_cast<const uint2 *>(a.links + n0);
     const bool in0 = lw.x == 0u, in1 = lw.y == 0u;
-    T g0[NS][9], g1[NS][9];
+    // pulled values of both nodes, kept packed in the storage type until
+    // they are used (for half: one register per plane for two nodes)
+    VS pk[NS][9];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
 #pragma unroll
@@ -423,24 +455,17 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
           e0 = v.x;
           e1 = v.y;
         }
-        S lo, hi;
         if (cx(i) == 0) {
-          lo = e0;
-          hi = e1;
+          pk[s][i] = pack2(e0, e1);
         } else if (cx(i) > 0) {  // sources x0 - 1, x0
           S left = __shfl_up_sync(0xffffffffu, e1, 1);
           if (lane == 0) left = (rowok && x0 >= 1) ? src[base - 1] : zero_of<S>();
-          lo = left;
-          hi = e0;
+          pk[s][i] = pack2(left, e0);
         } else {  // sources x0 + 1, x0 + 2
           S right = __shfl_down_sync(0xffffffffu, e0, 1);
           if (lane == 31) right = (rowok && x0 + 2 < a.nx_pad) ? src[base + 2] : zero_of<S>();
-          lo = e1;
-          hi = right;
+          pk[s][i] = pack2(e1, right);
         }
-        const T sh = adr_shift<P>(a, s, i);
-        g0[s][i] = P::load(lo) + sh;
-        g1[s][i] = P::load(hi) + sh;
       }
     }
     T *__restrict__ cpb = static_cast<T *>(a.cprev) + n0;
@@ -460,11 +485,15 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
       eq_factors<T>(ux.y, uy.y, E1);
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
+        T g0[9], g1[9];
         T c0 = T(0), c1 = T(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-          c0 += g0[s][i];
-          c1 += g1[s][i];
+          const T sh = adr_shift<P>(a, s, i);
+          g0[i] = P::load(pk[s][i].x) + sh;
+          g1[i] = P::load(pk[s][i].y) + sh;
+          c0 += g0[i];
+          c1 += g1[i];
         }
         const T om = pick<T>(a.omega[s], a.fomega[s]);
         if (in0 && in1) {
@@ -472,8 +501,8 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
           for (int i = 0; i < 9; ++i) {
             const T sh = adr_shift<P>(a, s, i);
             VS v;
-            v.x = P::store(g0[s][i] + om * (c0 * E0[i] - g0[s][i]) - sh);
-            v.y = P::store(g1[s][i] + om * (c1 * E1[i] - g1[s][i]) - sh);
+            v.x = P::store(g0[i] + om * (c0 * E0[i] - g0[i]) - sh);
+            v.y = P::store(g1[i] + om * (c1 * E1[i] - g1[i]) - sh);
             *reinterpret_cast<VS *>(dst + (long long)(s * 9 + i) * plane + n0) = v;
           }
         } else {
@@ -482,8 +511,8 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
           for (int i = 0; i < 9; ++i) {
             const T sh = adr_shift<P>(a, s, i);
             const long long o = (long long)(s * 9 + i) * plane + n0;
-            if (in0) dst[o] = P::store(g0[s][i] + om * (c0 * E0[i] - g0[s][i]) - sh);
-            if (in1) dst[o + 1] = P::store(g1[s][i] + om * (c1 * E1[i] - g1[s][i]) - sh);
+            if (in0) dst[o] = P::store(g0[i] + om * (c0 * E0[i] - g0[i]) - sh);
+            if (in1) dst[o + 1] = P::store(g1[i] + om * (c1 * E1[i] - g1[i]) - sh);
           }
         }
         if (MODE == kAdrCheck) {
@@ -869,12 +898,8 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
 #ifndef LBM_ADR_SPLIT
 #define LBM_ADR_SPLIT 1
 #endif
-// nodes per thread of the bulk kernel (1 or 2)
-#ifndef LBM_ADR_VEC
-#define LBM_ADR_VEC 1
-#endif
-inline dim3 adr_bulk_grid(int nx_pad, int ny) {
-  const int per = LBM_ADR_VEC * kBlockX;
+inline dim3 adr_bulk_grid(int vec, int nx_pad, int ny) {
+  const int per = vec * kBlockX;
   return dim3(static_cast<unsigned>((nx_pad + per - 1) / per),
               static_cast<unsigned>(ny));
 }
@@ -886,17 +911,24 @@ inline long long adr_list_blocks(long long nbnd) {
   return (nbnd + kBlockX - 1) / kBlockX;
 }
 // partial-sum rows written by one check step
-inline long long adr_partial_rows(int nx_pad, int ny, long long nbnd) {
+inline long long adr_partial_rows(int vec, int nx_pad, int ny, long long nbnd) {
   if (!LBM_ADR_SPLIT) {
     const dim3 g = adr_node_grid(nx_pad, ny);
     return static_cast<long long>(g.x) * g.y;
   }
-  const dim3 g = adr_bulk_grid(nx_pad, ny);
+  const dim3 g = adr_bulk_grid(vec, nx_pad, ny);
   return static_cast<long long>(g.x) * g.y + adr_list_blocks(nbnd);
 }
 
+// second stream and fork / join events for running the boundary-node kernel
+// beside the bulk kernel (aux == nullptr: one stream)
+struct AdrOverlap {
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
 template <class P>
-cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, cudaStream_t st);
+cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, cudaStream_t st,
+                       const AdrOverlap *ov = nullptr);
 template <class P>
 cudaError_t launch_adr_flux(int ns, const void *g, const uint32_t *links,
                             long long plane, int nx_pad, int ny, int xp,

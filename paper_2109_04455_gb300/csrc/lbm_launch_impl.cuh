@@ -8,7 +8,8 @@
 namespace lbm {
 
 template <class P, int NS>
-static cudaError_t launch_adr_ns(int mode, const AdrArgs &a, cudaStream_t st) {
+static cudaError_t launch_adr_ns(int mode, const AdrArgs &a, cudaStream_t st,
+                                 const AdrOverlap *ov) {
   const dim3 block(kBlockX);
   if (mode == kAdrInit) {
     adr_node_kernel<P, NS, kAdrInit, false>
@@ -24,26 +25,43 @@ static cudaError_t launch_adr_ns(int mode, const AdrArgs &a, cudaStream_t st) {
           <<<adr_node_grid(a.nx_pad, a.ny), block, 0, st>>>(a);
     return cudaGetLastError();
   }
-  const dim3 bg = adr_bulk_grid(a.nx_pad, a.ny);
+  const dim3 bg = adr_bulk_grid(P::kVec, a.nx_pad, a.ny);
   AdrArgs b = a;
   b.part_off = static_cast<long long>(bg.x) * bg.y;
   const unsigned lb = static_cast<unsigned>(adr_list_blocks(a.nbnd));
-  if (mode == kAdrStep) {
-    adr_bulk_kernel<P, NS, kAdrStep, LBM_ADR_VEC><<<bg, block, 0, st>>>(a);
-    if (lb) adr_node_kernel<P, NS, kAdrStep, true><<<lb, block, 0, st>>>(b);
-  } else {
-    adr_bulk_kernel<P, NS, kAdrCheck, LBM_ADR_VEC><<<bg, block, 0, st>>>(a);
-    if (lb) adr_node_kernel<P, NS, kAdrCheck, true><<<lb, block, 0, st>>>(b);
+  // The boundary nodes run on a second stream next to the bulk kernel when
+  // one is given: both read only the old populations and write disjoint
+  // nodes, so the few boundary blocks hide in the bulk kernel's time.
+  cudaStream_t sb = st;
+  cudaError_t e = cudaSuccess;
+  if (lb && ov && ov->aux) {
+    e = cudaEventRecord(ov->fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ov->aux, ov->fork, 0);
+    if (e != cudaSuccess) return e;
+    sb = ov->aux;
   }
-  return cudaGetLastError();
+  if (mode == kAdrStep) {
+    if (lb) adr_node_kernel<P, NS, kAdrStep, true><<<lb, block, 0, sb>>>(b);
+    adr_bulk_kernel<P, NS, kAdrStep, P::kVec><<<bg, block, 0, st>>>(a);
+  } else {
+    if (lb) adr_node_kernel<P, NS, kAdrCheck, true><<<lb, block, 0, sb>>>(b);
+    adr_bulk_kernel<P, NS, kAdrCheck, P::kVec><<<bg, block, 0, st>>>(a);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess && sb != st) {
+    e = cudaEventRecord(ov->join, sb);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ov->join, 0);
+  }
+  return e;
 }
 
 template <class P>
-cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, cudaStream_t st) {
+cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, cudaStream_t st,
+                       const AdrOverlap *ov) {
   switch (ns) {
-    case 1: return launch_adr_ns<P, 1>(mode, a, st);
-    case 2: return launch_adr_ns<P, 2>(mode, a, st);
-    case 3: return launch_adr_ns<P, 3>(mode, a, st);
+    case 1: return launch_adr_ns<P, 1>(mode, a, st, ov);
+    case 2: return launch_adr_ns<P, 2>(mode, a, st, ov);
+    case 3: return launch_adr_ns<P, 3>(mode, a, st, ov);
     default: return cudaErrorInvalidValue;
   }
 }

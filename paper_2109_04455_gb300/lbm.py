@@ -85,6 +85,13 @@ _SIGS = {
                                      _P]),
     "lbm_efficiency": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
     "lbm_adr_outflux_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "lbm_batch_ws_bytes": (ctypes.c_size_t, [ctypes.c_int32, _P, _P]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P,
+                                        ctypes.c_size_t, _P]),
+    "lbm_batch_destroy": (None, [_P]),
+    "lbm_batch_tune": (ctypes.c_int, [_P, _P, _P, _P]),
+    "lbm_batch_tuning": (ctypes.c_int, [_P, _P, _P, _P]),
+    "lbm_batch_solve": (ctypes.c_int, [_P, _P, _P]),
     "lbm_adr_adjoint_ws_bytes": (ctypes.c_size_t, [_P, _P]),
     "lbm_adr_adjoint": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double,
                                        ctypes.c_int32, _P, ctypes.c_size_t,
@@ -372,3 +379,62 @@ def lbm_adr_solve(geom: Geometry, params: lbm_adr_params, u, stream=None,
         _check(st)
     return conc, info.as_dict()
 
+
+# ---------------------------------------------------------------------------
+# batched solves
+# ---------------------------------------------------------------------------
+class Batch:
+    """lbm_batch_create / tune / solve over uploaded geometries, their ADR
+    parameters and device velocities (all lattices share nspecies and the
+    precision)."""
+
+    def __init__(self, geoms, params, us, device="cuda"):
+        lib = load()
+        self.geoms, self.us = list(geoms), list(us)
+        n = len(self.geoms)
+        self.count = n
+        self._g = (ctypes.c_void_p * n)(*[g.handle.value for g in self.geoms])
+        self._p = (lbm_adr_params * n)(*params)
+        self._u = (ctypes.c_void_p * n)(*[u.data_ptr() for u in self.us])
+        nbytes = lib.lbm_batch_ws_bytes(n, self._g, self._p)
+        if nbytes == 0:
+            raise LBMError(LBM_EINVAL, "lbm_batch_ws_bytes: invalid batch")
+        self.ws = _device_bytes(nbytes, device)
+        h = ctypes.c_void_p()
+        _check(lib.lbm_batch_create(n, self._g, self._p, self._u,
+                                    ctypes.c_void_p(self.ws.data_ptr()),
+                                    self.ws.numel(), ctypes.byref(h)))
+        self.handle = h
+
+    def tune(self, stream=None):
+        tile, grid = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().lbm_batch_tune(self.handle, _stream_ptr(stream),
+                                     ctypes.byref(tile), ctypes.byref(grid)))
+        return tile.value, grid.value
+
+    def tuning(self):
+        tile, grid = ctypes.c_int32(), ctypes.c_int32()
+        ms = (ctypes.c_float * 8)()
+        _check(load().lbm_batch_tuning(self.handle, ctypes.byref(tile),
+                                       ctypes.byref(grid), ms))
+        return dict(tile=tile.value, grid=grid.value,
+                    ms_per_step=[float(v) for v in ms])
+
+    def solve(self, stream=None, raise_not_converged: bool = False):
+        infos = (lbm_solve_info * self.count)()
+        st = load().lbm_batch_solve(self.handle, _stream_ptr(stream), infos)
+        if st != LBM_OK and not (st == LBM_ENOTCONVERGED and
+                                 not raise_not_converged):
+            _check(st)
+        return [i.as_dict() for i in infos]
+
+    def close(self):
+        if self.handle:
+            load().lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -16,7 +16,7 @@ from paper_2109_04455_gb300 import inputs, lbm  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
-PLANE = 3700        # just downstream of the first (A->B) membrane
+PLANE = 2730        # inside the first (A->B) membrane, where B is made
 STEPS = 2000
 
 
