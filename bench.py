@@ -50,6 +50,13 @@ def _args():
     ap.add_argument("--ny", type=int, default=4096)
     ap.add_argument("--fibers-per-band", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="large", choices=["large", "sweep"],
+                    help="large: the 67M-node membrane (default line); "
+                         "sweep: the 64-instance Pe x Da sweep, batched "
+                         "FP32 / FP16 against unbatched FP64 (solves/s)")
+    ap.add_argument("--sweep-instances", type=int, default=64)
+    ap.add_argument("--sweep-max-steps", type=int, default=5000)
+    ap.add_argument("--sweep-flow-steps", type=int, default=3000)
     return ap.parse_args()
 
 
@@ -423,10 +430,83 @@ def run_gpu(a):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Pe x Da sweep: batched reduced precision against unbatched FP64
+# ---------------------------------------------------------------------------
+def run_sweep(a):
+    """64 seeded lattices (Pe = logspace(-1,2,8) x Da = logspace(-2,2,8),
+    widths 512..2048, heights 256..512), each with its own flow (FP64, fixed
+    step count, untimed).  Timed: the ADR solves of all instances to their
+    residual tolerance (1e-6 reduced precision, 1e-9 FP64) or the step cap;
+    batched (one lbm_batch for all, FP32 and FP16 storage) against one
+    lbm_adr_solve per instance in FP64.  Reports solves/s and the largest
+    efficiency difference to FP64."""
+    import torch
+
+    from paper_2109_04455_gb300 import inputs, lbm
+    torch.cuda.set_device(0)
+    ws = [inputs.sweep_instance(i) for i in range(a.sweep_instances)]
+    geoms, u64 = [], []
+    for w in ws:
+        g = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
+        u, _ = lbm.lbm_flow_solve(g, w.tau_flow, w.u0, a.sweep_flow_steps,
+                                  precision=lbm.LBM_F64)
+        geoms.append(g)
+        u64.append(u)
+    nodes = sum(w.nx * w.ny for w in ws)
+    check = 500
+    cap = a.sweep_max_steps
+
+    def params(prec, tol):
+        return [lbm.adr_params(3, w.tau_c, precision=prec, max_steps=cap,
+                               tol=tol, check_every=check) for w in ws]
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+        enable_timing=True)
+    # unbatched FP64
+    p64 = params(lbm.LBM_F64, 1e-9)
+    torch.cuda.synchronize()
+    ev0.record()
+    ref = [lbm.lbm_adr_solve(g, p, u, want_conc=False)[1]
+           for g, p, u in zip(geoms, p64, u64)]
+    ev1.record()
+    torch.cuda.synchronize()
+    t64 = ev0.elapsed_time(ev1) * 1e-3
+    out = {"metric": "Pe x Da sweep solves/s (ADR, 3 species)",
+           "unit": "solves/s", "higher_is_better": True,
+           "instances": len(ws), "nodes": nodes, "step_cap": cap,
+           "check_every": check,
+           "f64_unbatched": {"solves_per_s": len(ws) / t64, "seconds": t64,
+                             "converged": sum(r["converged"] for r in ref),
+                             "steps": sum(r["steps"] for r in ref)}}
+    u32 = [u.float() for u in u64]
+    for name, prec in (("f32_batched", lbm.LBM_F32),
+                       ("f16dev_batched", lbm.LBM_F16DEV)):
+        b = lbm.Batch(geoms, params(prec, 1e-6), u32)
+        tile, grid = b.tune()
+        torch.cuda.synchronize()
+        ev0.record()
+        infos = b.solve()
+        ev1.record()
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) * 1e-3
+        de = max(abs(i["eps"] - r["eps"]) for i, r in zip(infos, ref))
+        out[name] = {"solves_per_s": len(ws) / t, "seconds": t,
+                     "speedup_vs_f64": t64 / t,
+                     "max_abs_eps_err_vs_f64": de,
+                     "converged": sum(i["converged"] for i in infos),
+                     "steps": sum(i["steps"] for i in infos),
+                     "tile": tile, "grid": grid}
+        b.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "sweep":
+        run_sweep(a)
     else:
         run_gpu(a)
 

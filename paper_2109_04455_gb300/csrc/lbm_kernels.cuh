@@ -26,29 +26,34 @@ namespace lbm {
 
 // Launch shape of the lattice kernels (compile-time tuning knobs):
 //   LBM_BLOCK_X        threads per block = nodes of one row segment
-//   LBM_ADR_MIN_BLOCKS resident blocks per SM asked of the register allocator
+//   LBM_ADR_MIN_BLOCKS if defined, resident blocks per SM asked of the
+//                      register allocator for every precision (otherwise
+//                      each precision's kMinBlocks below)
 #ifndef LBM_BLOCK_X
 #define LBM_BLOCK_X 256
 #endif
-#ifndef LBM_ADR_MIN_BLOCKS
-#define LBM_ADR_MIN_BLOCKS 1
-#endif
 constexpr int kBlockX = LBM_BLOCK_X;
+#ifdef LBM_ADR_MIN_BLOCKS
+#define LBM_MIN_BLOCKS(P) LBM_ADR_MIN_BLOCKS
+#else
+#define LBM_MIN_BLOCKS(P) P::kMinBlocks
+#endif
 constexpr int kReduceThreads = 256;
 
 // ---------------------------------------------------------------------------
 // precision traits: storage type S, compute type T
 // ---------------------------------------------------------------------------
-// nodes per thread of the bulk step (LBM_ADR_VEC_F16 overrides the half
-// path's choice; two nodes keep twice the bytes of 2-byte loads in flight)
+// nodes per thread of the bulk step of the half path (1 measured fastest:
+// the two-node form needs too many registers for the occupancy it loses)
 #ifndef LBM_ADR_VEC_F16
-#define LBM_ADR_VEC_F16 2
+#define LBM_ADR_VEC_F16 1
 #endif
 struct PrecF64 {
   using S = double;
   using T = double;
   static constexpr bool kDev = false;
   static constexpr int kVec = 1;
+  static constexpr int kMinBlocks = 1;
   static __device__ __forceinline__ T load(S v) { return v; }
   static __device__ __forceinline__ S store(T v) { return v; }
 };
@@ -57,17 +62,26 @@ struct PrecF32 {
   using T = float;
   static constexpr bool kDev = false;
   static constexpr int kVec = 1;
+  static constexpr int kMinBlocks = 1;
   static __device__ __forceinline__ T load(S v) { return v; }
   static __device__ __forceinline__ S store(T v) { return v; }
 };
-// half storage of the deviation g - w_i c_ref (round to nearest even)
+// half storage of the deviation g - w_i c_ref, scaled by 2^14 (exact) so that
+// the small populations of dilute species stay in half's normal range
+// (|value| <= 0.45 * 2^14 < 65504; the normal range then starts near 4e-9
+// instead of 6e-5), rounded to nearest even
 struct PrecF16Dev {
   using S = __half;
   using T = float;
   static constexpr bool kDev = true;
   static constexpr int kVec = LBM_ADR_VEC_F16;
-  static __device__ __forceinline__ T load(S v) { return __half2float(v); }
-  static __device__ __forceinline__ S store(T v) { return __float2half_rn(v); }
+  static constexpr int kMinBlocks = 5;   // <= 51 registers, 40 warps per SM
+  static __device__ __forceinline__ T load(S v) {
+    return __half2float(v) * (1.0f / 16384.0f);
+  }
+  static __device__ __forceinline__ S store(T v) {
+    return __float2half_rn(v * 16384.0f);
+  }
 };
 
 template <typename T>
@@ -374,7 +388,7 @@ __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
 // only the boundary nodes of a.bnodes, after the bulk kernel (below) has
 // updated the interior nodes; its partial sums go to rows a.part_off + block.
 template <class P, int NS, int MODE, bool LIST>
-__global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
+__global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
     adr_node_kernel(const AdrArgs a) {
   using T = typename P::T;
   long long n;
@@ -411,7 +425,7 @@ __global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
 // outside the lattice rows or row ends are skipped, so all accesses stay in
 // bounds; their values only reach nodes the boundary kernel rewrites.
 template <class P, int NS, int MODE, int VEC>
-__global__ void __launch_bounds__(kBlockX, LBM_ADR_MIN_BLOCKS)
+__global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
     adr_bulk_kernel(const AdrArgs a) {
   using S = typename P::S;
   using T = typename P::T;

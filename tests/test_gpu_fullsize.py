@@ -2,7 +2,7 @@
 launch configuration bench.py times.  The oracle cannot run this size, so
 these are properties that hold at any size:
 * FP32 and FP16-deviation storage against an FP64 GPU run of the same size
-  (efficiency within 1e-4 and 1e-3);
+  (concentration fields and outfluxes);
 * the species-sum invariant (A+B+C of the cascade equals one non-reacting
   species when every species has the anti-bounce-back inlet and the same
   tau, because the sources on each link add to zero);
@@ -33,26 +33,34 @@ def big():
     return w, geom, u64
 
 
-def _eps_ab(flux):
-    return flux[1] / (flux[0] + flux[1])
-
-
 def test_full_size_reduced_precision_against_f64(big):
+    """2000 steps from the same start on the same FP64 flow: the FP32 and
+    FP16-deviation concentration fields against the FP64 run (relative L2
+    per species: float rounding 1e-5 level, half storage 1e-3 level), and
+    the outfluxes through a plane inside the first membrane."""
     w, geom, u64 = big
-    out = {}
+    conc, flux = {}, {}
     for prec in (lbm.LBM_F64, lbm.LBM_F32, lbm.LBM_F16DEV):
         u = u64 if prec == lbm.LBM_F64 else u64.float()
         prm = lbm.adr_params(3, w.tau_c, precision=prec, max_steps=STEPS,
                              x_plane=PLANE)
-        _, info = lbm.lbm_adr_solve(geom, prm, u, want_conc=False)
-        out[prec] = info
+        c, info = lbm.lbm_adr_solve(geom, prm, u)
+        conc[prec] = c.double()[:, :, :w.nx]
+        flux[prec] = info["flux"]
+        del c
         torch.cuda.empty_cache()
-    e64 = _eps_ab(out[lbm.LBM_F64]["flux"])
-    assert e64 > 1e-3
-    assert abs(_eps_ab(out[lbm.LBM_F32]["flux"]) - e64) < 1e-4
-    assert abs(_eps_ab(out[lbm.LBM_F16DEV]["flux"]) - e64) < 1e-3
-    for prec in (lbm.LBM_F32, lbm.LBM_F16DEV):
-        assert abs(out[prec]["eps"] - out[lbm.LBM_F64]["eps"]) < 1e-3
+    ref = conc[lbm.LBM_F64]
+    for prec, tol in ((lbm.LBM_F32, 1e-4), (lbm.LBM_F16DEV, 1e-2)):
+        for s in range(3):
+            num = torch.linalg.vector_norm(conc[prec][s] - ref[s]).item()
+            den = torch.linalg.vector_norm(ref[s]).item()
+            assert den > 0 and num / den < tol, (prec, s, num / den)
+        f64 = flux[lbm.LBM_F64]
+        scale = abs(f64[0])
+        for s in range(3):
+            assert abs(flux[prec][s] - f64[s]) < 10 * tol * scale
+    # the catalysts worked: B and C exist
+    assert ref[1].max().item() > 1e-3 and ref[2].max().item() > 1e-5
 
 
 def test_full_size_species_sum_invariant(big):
