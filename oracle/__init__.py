@@ -62,7 +62,7 @@ CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
 
 def build_command(out=_LIB):
     return ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c99",
-            _SRC, "-o", out, "-lm"]
+            "-fopenmp", _SRC, "-o", out, "-lm"]
 
 
 def build(force: bool = False) -> str:
@@ -106,8 +106,14 @@ def _load():
             lib.orc_adr_gradient.argtypes = [I, I, I, P, P, P, P, P, P, I, P,
                                              I, P, P, P, P]
             lib.orc_fiber_ids.argtypes = [I, I, I, P, P]
+            lib.orc_num_threads.restype = I
             _lib = lib
     return _lib
+
+
+def num_threads() -> int:
+    """Threads the oracle's time steps run on."""
+    return int(_load().orc_num_threads())
 
 
 def _p(a: np.ndarray):

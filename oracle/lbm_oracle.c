@@ -28,13 +28,19 @@
  * (0,1), (-1,0), (0,-1); c_5..c_8 = (1,1), (-1,1), (-1,-1), (1,-1).
  * Weights 4/9, 1/9, 1/36; c_s^2 = 1/3.
  *
- * Compile: gcc -O2 -ffp-contract=off -fPIC -shared (no fused multiply-add, so
- * every product and sum is rounded exactly as written).
+ * Compile: gcc -O2 -ffp-contract=off -fPIC -shared -fopenmp (no fused
+ * multiply-add, so every product and sum is rounded exactly as written).
+ * The time steps split the lattice rows over OpenMP threads; every node's
+ * update is independent and each output slot is written by exactly one
+ * node, so the result does not depend on the thread count.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q9 9
 
@@ -170,6 +176,7 @@ void orc_flow_moments(int nx, int ny, const uint8_t *solid, const double *f,
  * The x-boundary rule wins over the wall rule on corner links. */
 static void flow_step(int nx, int ny, const uint8_t *solid, double tau,
                       double u0, int flags, const double *f, double *fn) {
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y) {
     for (int x = 0; x < nx; ++x) {
       long n = (long)y * nx + x;
@@ -332,8 +339,9 @@ static void adr_step(int nx, int ny, int ns, const uint8_t *solid,
                      const double *uy, const double *tau, const double *cin,
                      int flags, const double *g, double *gn) {
   long nn = (long)nx * ny;
-  double gs[3][Q9];
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < ny; ++y) {
+    double gs[3][Q9];
     for (int x = 0; x < nx; ++x) {
       long n = (long)y * nx + x;
       if (solid[n]) continue;
@@ -520,9 +528,10 @@ int orc_adr_adjoint_steps(int nx, int ny, int ns, const uint8_t *solid,
   long nt = (long)ns * nn * Q9;
   memset(tmp, 0, sizeof(double) * nt);
   double *a = nu, *b = tmp;
-  double mu[3][Q9];
   for (long step = 0; step < nsteps; ++step) {
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y) {
+      double mu[3][Q9];
       for (int x = 0; x < nx; ++x) {
         long n = (long)y * nx + x;
         if (solid[n]) continue;
@@ -619,4 +628,13 @@ void orc_fiber_ids(int nx, int ny, int nfib, const double *fib, int32_t *ids) {
         }
       }
     }
+}
+
+/* Threads the time steps use (1 without OpenMP). */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }

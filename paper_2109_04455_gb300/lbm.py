@@ -420,11 +420,14 @@ class Batch:
         return dict(tile=tile.value, grid=grid.value,
                     ms_per_step=[float(v) for v in ms])
 
-    def solve(self, stream=None, raise_not_converged: bool = False):
+    def solve(self, stream=None, strict: bool = False):
+        """Solve every lattice; returns one info dict per lattice.  A lattice
+        that stopped at its step cap (converged False) or went non-finite
+        (residual NaN) is reported in its info; strict=True raises instead."""
         infos = (lbm_solve_info * self.count)()
         st = load().lbm_batch_solve(self.handle, _stream_ptr(stream), infos)
-        if st != LBM_OK and not (st == LBM_ENOTCONVERGED and
-                                 not raise_not_converged):
+        if st != LBM_OK and (strict or st not in (LBM_ENOTCONVERGED,
+                                                  LBM_EUNSTABLE)):
             _check(st)
         return [i.as_dict() for i in infos]
 

@@ -299,3 +299,49 @@ def test_workspace_too_small_and_not_converged():
     with pytest.raises(lbm.LBMError) as e:
         lbm.lbm_adr_solve(geom, prm, u, raise_not_converged=True)
     assert e.value.status == lbm.LBM_ENOTCONVERGED
+
+
+# ---------------------------------------------------------------------------
+# the two-membrane cascade lattice in full size (2048 x 512, 80 fibers, Pe = 1),
+# at a fixed step count the oracle (OpenMP over rows) finishes in a minute or
+# two; the flux plane sits just downstream of the A->B membrane
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def cascade_oracle():
+    w = inputs.two_membrane_cascade(seed=0, pe=1.0)
+    nflow, nadr, xp = 2000, 2000, 720
+    solid, kab, kbc = oracle.raster(w.nx, w.ny, w.fibers, w.k1, w.k2)
+    _, ux, uy, _ = oracle.flow_run(solid, w.tau_flow, w.u0, nflow)
+    prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, [w.tau_c] * 3,
+                             [1, 0, 0])
+    ref = prob.run(nadr, xp=xp)
+    return w, ux, uy, ref, nflow, nadr, xp
+
+
+def test_cascade_full_lattice_f64(cascade_oracle):
+    w, ux, uy, ref, nflow, nadr, xp = cascade_oracle
+    geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
+    u, _ = lbm.lbm_flow_solve(geom, w.tau_flow, w.u0, nflow,
+                              precision=lbm.LBM_F64)
+    ug = u.cpu().numpy()[:, :, :w.nx]
+    assert np.abs(ug[0] - ux).max() < 1e-12 and np.abs(ug[1] - uy).max() < 1e-12
+    conc, info = _run_gpu_adr(geom, u, 3, [w.tau_c] * 3, [1, 0, 0],
+                              lbm.LBM_F64, nadr, xp=xp)
+    rel = np.linalg.norm(conc - ref["conc"]) / np.linalg.norm(ref["conc"])
+    assert rel < 1e-10
+    assert np.allclose(info["flux"], ref["flux"], rtol=1e-10, atol=1e-15)
+    assert ref["flux"][1] > 1e-4          # B crosses the plane
+
+
+@pytest.mark.parametrize("prec,tol", [(lbm.LBM_F32, 1e-4),
+                                      (lbm.LBM_F16DEV, 1e-3)])
+def test_cascade_full_lattice_reduced(cascade_oracle, prec, tol):
+    w, ux, uy, ref, nflow, nadr, xp = cascade_oracle
+    geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
+    u = _dev_u(ux, uy, geom.nx_pad, torch.float32)
+    _, info = _run_gpu_adr(geom, u, 3, [w.tau_c] * 3, [1, 0, 0], prec, nadr,
+                           xp=xp)
+    e_ref = oracle.efficiency(ref["flux"][:2], 2)
+    e_gpu = lbm.lbm_efficiency(list(info["flux"][:2]) + [0.0], 2)
+    assert e_ref > 10 * tol
+    assert abs(e_gpu - e_ref) < tol
