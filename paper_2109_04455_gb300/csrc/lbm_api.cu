@@ -442,6 +442,8 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
   a.bnodes = g->d_bnodes;
   a.nbnd = static_cast<long long>(g->bnodes.size());
   a.part_off = 0;
+  // status word of the TMA-staged step (last double slot of the results)
+  a.status = reinterpret_cast<int *>(s->result + 15);
   a.plane = plane_of(g);
   a.nx = g->nx;
   a.ny = g->ny;
@@ -489,6 +491,7 @@ extern "C" lbm_status lbm_adr_init(lbm_adr_solver *s, void *stream) {
   cudaStream_t st = as_stream(stream);
   const AdrLayout l = adr_layout(s->g, &s->p);
   cudaError_t e = cudaMemsetAsync(s->buf[0], 0, 2 * l.buf + l.cprev, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->result, 0, 16 * sizeof(double), st);
   if (e != cudaSuccess) return cuda_fail("lbm_adr_init", e);
   AdrArgs a = s->a;
   a.src = nullptr;
@@ -538,6 +541,12 @@ extern "C" lbm_status lbm_adr_run(lbm_adr_solver *s, int64_t nsteps,
   s->has_check = true;
   std::memset(info, 0, sizeof(*info));
   info->steps = s->steps;
+  int status_word = 0;
+  std::memcpy(&status_word, &h[15], sizeof(int));
+  if (status_word != 0) {
+    set_error("lbm_adr_run: a staged copy did not complete in time");
+    return LBM_ECUDA;
+  }
   bool finite = true;
   double r = 0.0;
   for (int k = 0; k < ns; ++k) {

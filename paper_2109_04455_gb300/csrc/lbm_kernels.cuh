@@ -180,6 +180,7 @@ struct AdrArgs {
   long long part_off;       // first partial row of the boundary kernel
   long long plane;          // ny * nx_pad
   int nx, ny, nx_pad;
+  int *status;              // device word: non-zero after a failed wait
   int abb_all;              // anti-bounce-back inlet for every species
   int xp;                   // flux plane
   double omega[3];          // 1/tau per species

@@ -3,9 +3,47 @@
 // the kernel variants compile in parallel.
 #pragma once
 
+#include <mutex>
+
 #include "lbm_kernels.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbm {
+
+// Persistent grid of the TMA-staged step: resident blocks per SM x SMs of
+// the current device (the shared-memory limit is raised once per kernel).
+template <class P, int NS, int MODE>
+static unsigned tma_grid(long long ntiles) {
+  using L = TmaLayout<P, NS>;
+  static std::once_flag once;
+  static int per_sm = 1;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(adr_tma_kernel<P, NS, MODE>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(L::kBytes));
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nb, adr_tma_kernel<P, NS, MODE>, kBlockX, L::kBytes);
+    per_sm = nb > 0 ? nb : 1;
+  });
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long g = static_cast<long long>(per_sm) * sms;
+  return static_cast<unsigned>(g < ntiles ? g : (ntiles > 0 ? ntiles : 1));
+}
+
+template <class P, int NS, int MODE>
+static void launch_bulk(const AdrArgs &a, dim3 bg, cudaStream_t st) {
+  if (adr_uses_tma<P>() && a.status != nullptr) {
+    using L = TmaLayout<P, NS>;
+    const long long ntiles = static_cast<long long>(bg.x) * bg.y;
+    adr_tma_kernel<P, NS, MODE>
+        <<<tma_grid<P, NS, MODE>(ntiles), kBlockX, L::kBytes, st>>>(a, a.status);
+  } else {
+    adr_bulk_kernel<P, NS, MODE, P::kVec><<<bg, dim3(kBlockX), 0, st>>>(a);
+  }
+}
 
 template <class P, int NS>
 static cudaError_t launch_adr_ns(int mode, const AdrArgs &a, cudaStream_t st,
@@ -42,10 +80,10 @@ static cudaError_t launch_adr_ns(int mode, const AdrArgs &a, cudaStream_t st,
   }
   if (mode == kAdrStep) {
     if (lb) adr_node_kernel<P, NS, kAdrStep, true><<<lb, block, 0, sb>>>(b);
-    adr_bulk_kernel<P, NS, kAdrStep, P::kVec><<<bg, block, 0, st>>>(a);
+    launch_bulk<P, NS, kAdrStep>(a, bg, st);
   } else {
     if (lb) adr_node_kernel<P, NS, kAdrCheck, true><<<lb, block, 0, sb>>>(b);
-    adr_bulk_kernel<P, NS, kAdrCheck, P::kVec><<<bg, block, 0, st>>>(a);
+    launch_bulk<P, NS, kAdrCheck>(a, bg, st);
   }
   e = cudaGetLastError();
   if (e == cudaSuccess && sb != st) {
