@@ -175,9 +175,10 @@ def _ncu_traffic(precision: str, units_per_launch: int):
 
 
 def _algorithmic_bytes(geom, w, precision):
-    """Bytes one ADR step launch must move: per fluid node 3 species x 9
-    populations read + written, the velocity (2 values) and the link word;
-    per solid node its link word; the rates of each catalytic link (two
+    """Bytes one ADR step must move: per fluid node 3 species x 9
+    populations read + written, the velocity (2 values) and the link word
+    (half storage: also each species' float reference, read + written); per
+    solid node its link word; the rates of each catalytic link (two
     doubles)."""
     import numpy as np
     import torch
@@ -192,6 +193,8 @@ def _algorithmic_bytes(geom, w, precision):
     for j in range(8):
         ncat += int((((fl >> (4 * j)) & 0xF) == 3).sum())
     per_fluid = SPECIES * 9 * 2 * es + 2 * ue + 4
+    if precision == "f16dev":
+        per_fluid += SPECIES * 2 * 4   # per-node reference, read + written
     total = n_fluid * per_fluid + n_solid * 4 + ncat * 16
     return total, n_fluid, per_fluid
 

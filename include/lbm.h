@@ -50,8 +50,9 @@ typedef enum {
 typedef enum {
   LBM_F64 = 0,    /* populations stored and computed in double              */
   LBM_F32 = 1,    /* populations stored and computed in float               */
-  LBM_F16DEV = 2  /* populations stored in half as g - w_i*c_ref,s (c_ref =
-                     inlet concentration of the species), computed in float */
+  LBM_F16DEV = 2  /* populations stored in half as (g - w_i*R) * 2^14, R the
+                     concentration of the storing node (kept in float beside
+                     them); computed in float */
 } lbm_precision;
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -4,8 +4,8 @@
 namespace lbm {
 template cudaError_t launch_adr<PrecF16Dev>(int, int, const AdrArgs &,
                                             cudaStream_t, const AdrOverlap *);
-template cudaError_t launch_adr_flux<PrecF16Dev>(int, const void *,
+template cudaError_t launch_adr_flux<PrecF16Dev>(int, const void *, const float *,
                                                  const uint32_t *, long long,
-                                                 int, int, int, const double *,
-                                                 double *, cudaStream_t);
+                                                 int, int, int, double *,
+                                                 cudaStream_t);
 }  // namespace lbm

@@ -4,10 +4,10 @@
 namespace lbm {
 template cudaError_t launch_adr<PrecF32>(int, int, const AdrArgs &,
                                             cudaStream_t, const AdrOverlap *);
-template cudaError_t launch_adr_flux<PrecF32>(int, const void *,
+template cudaError_t launch_adr_flux<PrecF32>(int, const void *, const float *,
                                                  const uint32_t *, long long,
-                                                 int, int, int, const double *,
-                                                 double *, cudaStream_t);
+                                                 int, int, int, double *,
+                                                 cudaStream_t);
 template cudaError_t launch_flow<PrecF32>(int, const FlowArgs &, dim3,
                                              cudaStream_t);
 template cudaError_t launch_adjoint<PrecF32>(int, int, const AdjArgs &,

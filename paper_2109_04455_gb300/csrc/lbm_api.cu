@@ -69,10 +69,6 @@ size_t store_bytes(int prec) {
   return prec == LBM_F64 ? 8 : (prec == LBM_F32 ? 4 : 2);
 }
 size_t compute_bytes(int prec) { return prec == LBM_F64 ? 8 : 4; }
-int prec_vec(int prec) {
-  return prec == LBM_F64 ? PrecF64::kVec
-                         : (prec == LBM_F32 ? PrecF32::kVec : PrecF16Dev::kVec);
-}
 
 // Make the device that owns `p` current for this thread (the caller's
 // buffers decide where the work runs); rejects host memory.
@@ -309,6 +305,7 @@ struct lbm_adr_solver {
   double *partials = nullptr;
   double *scratch = nullptr;
   double *result = nullptr;
+  float *rbuf[2] = {nullptr, nullptr};  // reference concentrations (half)
   int cur = 0;
   int64_t steps = 0;
   bool has_check = false;
@@ -317,7 +314,7 @@ struct lbm_adr_solver {
 };
 
 struct AdrLayout {
-  size_t buf, cprev, partials, scratch, result, total;
+  size_t buf, cprev, partials, scratch, result, ref, total;
 };
 
 static AdrLayout adr_layout(const lbm_geometry *g, const lbm_adr_params *p) {
@@ -327,12 +324,14 @@ static AdrLayout adr_layout(const lbm_geometry *g, const lbm_adr_params *p) {
   l.buf = align256(ns * 9 * pl * store_bytes(p->precision));
   l.cprev = align256(ns * pl * compute_bytes(p->precision));
   l.partials = align256(static_cast<size_t>(adr_partial_rows(
-                            prec_vec(p->precision), g->nx_pad, g->ny,
+                            g->nx_pad, g->ny,
                             static_cast<long long>(g->bnodes.size()))) *
                         2 * ns * 8);
   l.scratch = align256(kReduceGrid * 2 * ns * 8);
   l.result = align256(64 * 8);
-  l.total = 2 * l.buf + l.cprev + l.partials + l.scratch + l.result;
+  // half storage: per-node reference concentrations of both buffers
+  l.ref = p->precision == LBM_F16DEV ? align256(ns * pl * 4) : 0;
+  l.total = 2 * l.buf + l.cprev + l.partials + l.scratch + l.result + 2 * l.ref;
   return l;
 }
 
@@ -363,18 +362,19 @@ static cudaError_t adr_flux_launch(const lbm_adr_solver *s, cudaStream_t st) {
   const lbm_geometry *g = s->g;
   int xp = s->p.x_plane < 0 ? g->nx - 3 : s->p.x_plane;
   const void *cur = s->buf[s->cur];
+  const float *ref = s->rbuf[s->cur];
   double *out = s->result + 8;
   const int ns = s->p.nspecies;
   switch (s->p.precision) {
     case LBM_F64:
-      return launch_adr_flux<PrecF64>(ns, cur, g->d_links, plane_of(g), g->nx_pad,
-                                      g->ny, xp, s->a.cref, out, st);
+      return launch_adr_flux<PrecF64>(ns, cur, ref, g->d_links, plane_of(g),
+                                      g->nx_pad, g->ny, xp, out, st);
     case LBM_F32:
-      return launch_adr_flux<PrecF32>(ns, cur, g->d_links, plane_of(g), g->nx_pad,
-                                      g->ny, xp, s->a.cref, out, st);
+      return launch_adr_flux<PrecF32>(ns, cur, ref, g->d_links, plane_of(g),
+                                      g->nx_pad, g->ny, xp, out, st);
     default:
-      return launch_adr_flux<PrecF16Dev>(ns, cur, g->d_links, plane_of(g),
-                                         g->nx_pad, g->ny, xp, s->a.cref, out, st);
+      return launch_adr_flux<PrecF16Dev>(ns, cur, ref, g->d_links, plane_of(g),
+                                         g->nx_pad, g->ny, xp, out, st);
   }
 }
 
@@ -430,7 +430,12 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
   s->scratch = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials);
   s->result = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials +
                                          l.scratch);
-  s->nb = adr_partial_rows(prec_vec(p->precision), g->nx_pad, g->ny,
+  if (l.ref) {
+    char *rb = b + 2 * l.buf + l.cprev + l.partials + l.scratch + l.result;
+    s->rbuf[0] = reinterpret_cast<float *>(rb);
+    s->rbuf[1] = reinterpret_cast<float *>(rb + l.ref);
+  }
+  s->nb = adr_partial_rows(g->nx_pad, g->ny,
                            static_cast<long long>(g->bnodes.size()));
   AdrArgs &a = s->a;
   a.links = g->d_links;
@@ -453,10 +458,8 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
     const bool on = k < p->nspecies;
     a.omega[k] = on ? 1.0 / p->tau[k] : 0.0;
     a.cin[k] = on ? p->c_in[k] : 0.0;
-    a.cref[k] = (on && p->precision == LBM_F16DEV) ? p->c_in[k] : 0.0;
     a.fomega[k] = static_cast<float>(a.omega[k]);
     a.fcin[k] = static_cast<float>(a.cin[k]);
-    a.fcref[k] = static_cast<float>(a.cref[k]);
   }
   // second stream for the boundary-node kernel (no device memory involved)
   if (!g->bnodes.empty()) {
@@ -492,10 +495,13 @@ extern "C" lbm_status lbm_adr_init(lbm_adr_solver *s, void *stream) {
   const AdrLayout l = adr_layout(s->g, &s->p);
   cudaError_t e = cudaMemsetAsync(s->buf[0], 0, 2 * l.buf + l.cprev, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->result, 0, 16 * sizeof(double), st);
+  if (e == cudaSuccess && l.ref) e = cudaMemsetAsync(s->rbuf[0], 0, 2 * l.ref, st);
   if (e != cudaSuccess) return cuda_fail("lbm_adr_init", e);
   AdrArgs a = s->a;
   a.src = nullptr;
   a.dst = s->buf[0];
+  a.rsrc = nullptr;
+  a.rdst = s->rbuf[0];
   e = adr_launch(s->p.precision, s->p.nspecies, kAdrInit, a, st);
   if (e != cudaSuccess) return cuda_fail("lbm_adr_init(kernel)", e);
   s->cur = 0;
@@ -508,6 +514,8 @@ static cudaError_t adr_step(lbm_adr_solver *s, int mode, cudaStream_t st) {
   AdrArgs a = s->a;
   a.src = s->buf[s->cur];
   a.dst = s->buf[s->cur ^ 1];
+  a.rsrc = s->rbuf[s->cur];
+  a.rdst = s->rbuf[s->cur ^ 1];
   s->cur ^= 1;
   ++s->steps;
   return adr_launch(s->p.precision, s->p.nspecies, mode, a, st, &s->ov);
@@ -879,13 +887,11 @@ static double *g_addr[256] = {};  // device address of the array, per device
 // all three slots, so nothing has to start at zero.
 template <class P, int NS>
 __global__ void __launch_bounds__(kRowsPerBlock)
-    outflux_partial_noalloc_kernel(const void *g, const uint32_t *links,
-                                   long long plane, int nx_pad, int ny, int xp,
-                                   double cref0, double cref1, double cref2,
-                                   double *part) {
+    outflux_partial_noalloc_kernel(const void *g, const float *ref,
+                                   const uint32_t *links, long long plane,
+                                   int nx_pad, int ny, int xp, double *part) {
   using S = typename P::S;
   const S *src = static_cast<const S *>(g);
-  const double cref[3] = {cref0, cref1, cref2};
   const int y = blockIdx.x * kRowsPerBlock + threadIdx.x;
   double acc[3] = {0.0, 0.0, 0.0};
   if (y < ny) {
@@ -897,7 +903,7 @@ __global__ void __launch_bounds__(kRowsPerBlock)
         for (int i = 1; i < 9; ++i) {
           if (cx(i) == 0) continue;
           double gi = double(P::load(src[(long long)(s * 9 + i) * plane + n]));
-          if (P::kDev) gi += double(Lattice<float>::w(i)) * cref[s];
+          if (P::kDev) gi += double(Lattice<float>::w(i)) * double(ref[s * plane + n]);
           acc[s] += cx(i) > 0 ? gi : -gi;
         }
       }
@@ -921,24 +927,24 @@ __global__ void __launch_bounds__(kReduceThreads)
 }
 
 template <class P>
-cudaError_t outflux_noalloc_launch(int ns, const void *g, const uint32_t *links,
-                                   long long plane, int nx_pad, int ny, int xp,
-                                   const double *cref, double *scratch,
+cudaError_t outflux_noalloc_launch(int ns, const void *g, const float *ref,
+                                   const uint32_t *links, long long plane,
+                                   int nx_pad, int ny, int xp, double *scratch,
                                    cudaStream_t st) {
   const int nb = (ny + kRowsPerBlock - 1) / kRowsPerBlock;
   const dim3 block(kRowsPerBlock);
   switch (ns) {
     case 1:
       outflux_partial_noalloc_kernel<P, 1><<<nb, block, 0, st>>>(
-          g, links, plane, nx_pad, ny, xp, cref[0], cref[1], cref[2], scratch);
+          g, ref, links, plane, nx_pad, ny, xp, scratch);
       break;
     case 2:
       outflux_partial_noalloc_kernel<P, 2><<<nb, block, 0, st>>>(
-          g, links, plane, nx_pad, ny, xp, cref[0], cref[1], cref[2], scratch);
+          g, ref, links, plane, nx_pad, ny, xp, scratch);
       break;
     default:
       outflux_partial_noalloc_kernel<P, 3><<<nb, block, 0, st>>>(
-          g, links, plane, nx_pad, ny, xp, cref[0], cref[1], cref[2], scratch);
+          g, ref, links, plane, nx_pad, ny, xp, scratch);
       break;
   }
   outflux_final_noalloc_kernel<<<1, dim3(kReduceThreads), 0, st>>>(
@@ -993,19 +999,19 @@ extern "C" lbm_status lbm_adr_outflux_noalloc(lbm_adr_solver *s,
   const int ns = s->p.nspecies;
   switch (s->p.precision) {
     case LBM_F64:
-      e = noalloc::outflux_noalloc_launch<PrecF64>(ns, cur, g->d_links, plane_of(g),
-                                          g->nx_pad, g->ny, xp, s->a.cref,
-                                          scratch, st);
+      e = noalloc::outflux_noalloc_launch<PrecF64>(ns, cur, s->rbuf[s->cur], g->d_links,
+                                                   plane_of(g), g->nx_pad, g->ny, xp,
+                                                   scratch, st);
       break;
     case LBM_F32:
-      e = noalloc::outflux_noalloc_launch<PrecF32>(ns, cur, g->d_links, plane_of(g),
-                                          g->nx_pad, g->ny, xp, s->a.cref,
-                                          scratch, st);
+      e = noalloc::outflux_noalloc_launch<PrecF32>(ns, cur, s->rbuf[s->cur], g->d_links,
+                                                   plane_of(g), g->nx_pad, g->ny, xp,
+                                                   scratch, st);
       break;
     default:
-      e = noalloc::outflux_noalloc_launch<PrecF16Dev>(ns, cur, g->d_links, plane_of(g),
-                                             g->nx_pad, g->ny, xp, s->a.cref,
-                                             scratch, st);
+      e = noalloc::outflux_noalloc_launch<PrecF16Dev>(ns, cur, s->rbuf[s->cur], g->d_links,
+                                                   plane_of(g), g->nx_pad, g->ny, xp,
+                                                   scratch, st);
       break;
   }
   double h[3] = {0.0, 0.0, 0.0};

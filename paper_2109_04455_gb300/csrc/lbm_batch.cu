@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kReduceThreads)
       for (int i = 1; i < 9; ++i) {
         if (cx(i) == 0) continue;
         double gi = double(P::load(src[(long long)(s * 9 + i) * a.plane + n]));
-        if (P::kDev) gi += double(Lattice<float>::w(i)) * a.cref[s];
+        if (P::kDev) gi += double(Lattice<float>::w(i)) * double(a.rdst[s * a.plane + n]);
         v += cx(i) > 0 ? gi : -gi;
       }
       acc[s] += v;
@@ -247,6 +247,7 @@ struct BatchLayout {
   std::vector<size_t> inst_off;  // start of each instance's buffers
   std::vector<size_t> buf;       // bytes of one population buffer
   std::vector<size_t> cprev;
+  std::vector<size_t> ref;       // bytes of one reference buffer (half only)
 };
 
 BatchLayout batch_layout(int count, const lbm_geometry *const *geoms,
@@ -267,10 +268,12 @@ BatchLayout batch_layout(int count, const lbm_geometry *const *geoms,
     const size_t pl = static_cast<size_t>(geoms[i]->nx_pad) * geoms[i]->ny;
     const size_t b = a256(ns * 9 * pl * store_b(p[0].precision));
     const size_t c = a256(ns * pl * comp_b(p[0].precision));
+    const size_t r = p[0].precision == LBM_F16DEV ? a256(ns * pl * 4) : 0;
     l.inst_off.push_back(off);
     l.buf.push_back(b);
     l.cprev.push_back(c);
-    off += 2 * b + c;
+    l.ref.push_back(r);
+    off += 2 * b + c + 2 * r;
   }
   l.total = off;
   return l;
@@ -400,6 +403,8 @@ lbm_status init_states(lbm_batch *b, cudaStream_t st) {
     if (e == cudaSuccess) {
       a.src = nullptr;
       a.dst = const_cast<void *>(b->table[2 * i].src);  // initial state: buffer 0
+      a.rsrc = nullptr;
+      a.rdst = const_cast<float *>(b->table[2 * i].rsrc);
       switch (b->prec) {
         case LBM_F64: e = launch_adr<PrecF64>(b->ns, kAdrInit, a, st); break;
         case LBM_F32: e = launch_adr<PrecF32>(b->ns, kAdrInit, a, st); break;
@@ -502,16 +507,24 @@ extern "C" lbm_status lbm_batch_create(int32_t count,
       const bool on = k < p.nspecies;
       a.omega[k] = on ? 1.0 / p.tau[k] : 0.0;
       a.cin[k] = on ? p.c_in[k] : 0.0;
-      a.cref[k] = (on && p.precision == LBM_F16DEV) ? p.c_in[k] : 0.0;
       a.fomega[k] = static_cast<float>(a.omega[k]);
       a.fcin[k] = static_cast<float>(a.cin[k]);
-      a.fcref[k] = static_cast<float>(a.cref[k]);
+    }
+    float *ref0 = nullptr, *ref1 = nullptr;
+    if (l.ref[i]) {
+      char *rb = base + l.inst_off[i] + 2 * l.buf[i] + l.cprev[i];
+      ref0 = reinterpret_cast<float *>(rb);
+      ref1 = reinterpret_cast<float *>(rb + l.ref[i]);
     }
     a.src = buf0;
     a.dst = buf1;
+    a.rsrc = ref0;
+    a.rdst = ref1;
     b->table[2 * i] = a;
     a.src = buf1;
     a.dst = buf0;
+    a.rsrc = ref1;
+    a.rdst = ref0;
     b->table[2 * i + 1] = a;
   }
   cudaError_t e = cudaMemcpy(b->d_table, b->table.data(),

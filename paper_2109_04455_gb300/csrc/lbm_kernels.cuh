@@ -43,16 +43,10 @@ constexpr int kReduceThreads = 256;
 // ---------------------------------------------------------------------------
 // precision traits: storage type S, compute type T
 // ---------------------------------------------------------------------------
-// nodes per thread of the bulk step of the half path (1 measured fastest:
-// the two-node form needs too many registers for the occupancy it loses)
-#ifndef LBM_ADR_VEC_F16
-#define LBM_ADR_VEC_F16 1
-#endif
 struct PrecF64 {
   using S = double;
   using T = double;
   static constexpr bool kDev = false;
-  static constexpr int kVec = 1;
   static constexpr int kMinBlocks = 1;
   static __device__ __forceinline__ T load(S v) { return v; }
   static __device__ __forceinline__ S store(T v) { return v; }
@@ -61,20 +55,21 @@ struct PrecF32 {
   using S = float;
   using T = float;
   static constexpr bool kDev = false;
-  static constexpr int kVec = 1;
   static constexpr int kMinBlocks = 1;
   static __device__ __forceinline__ T load(S v) { return v; }
   static __device__ __forceinline__ S store(T v) { return v; }
 };
-// half storage of the deviation g - w_i c_ref, scaled by 2^14 (exact) so that
-// the small populations of dilute species stay in half's normal range
-// (|value| <= 0.45 * 2^14 < 65504; the normal range then starts near 4e-9
-// instead of 6e-5), rounded to nearest even
+// half storage of the deviation g - w_i R from a per-node reference R (the
+// node's concentration when the value was stored, kept in float beside the
+// populations), scaled by 2^14 (exact) so that the deviations of dilute
+// species stay in half's normal range (|value| <= 0.45 * 2^14 < 65504);
+// rounded to nearest even.  The deviation is the advective and
+// non-equilibrium part of g, a few percent of it, so half's 11 bits resolve
+// g to ~1e-5 instead of ~5e-4.
 struct PrecF16Dev {
   using S = __half;
   using T = float;
   static constexpr bool kDev = true;
-  static constexpr int kVec = LBM_ADR_VEC_F16;
   static constexpr int kMinBlocks = 5;   // <= 51 registers, 40 warps per SM
   static __device__ __forceinline__ T load(S v) {
     return __half2float(v) * (1.0f / 16384.0f);
@@ -147,9 +142,6 @@ __device__ __forceinline__ S zero_of() { return S(0); }
 template <>
 __device__ __forceinline__ __half zero_of<__half>() { return __float2half_rn(0.0f); }
 
-__device__ __forceinline__ double2 pack2(double lo, double hi) { return make_double2(lo, hi); }
-__device__ __forceinline__ float2 pack2(float lo, float hi) { return make_float2(lo, hi); }
-__device__ __forceinline__ __half2 pack2(__half lo, __half hi) { return __halves2half2(lo, hi); }
 
 // Kernel parameters come in double and in float; the float paths read the
 // float copy, so no thread converts a double (this part's FP64 pipe is
@@ -185,24 +177,41 @@ struct AdrArgs {
   int xp;                   // flux plane
   double omega[3];          // 1/tau per species
   double cin[3];            // inlet concentration per species
-  double cref[3];           // reference concentration of the stored deviation
-  float fomega[3], fcin[3], fcref[3];  // the same in float
+  float fomega[3], fcin[3]; // the same in float
+  // half storage: reference concentrations [ns][plane] of the src and dst
+  // populations (the stored value is g - w_i R of its node)
+  const float *rsrc;
+  float *rdst;
 };
 
 enum AdrMode { kAdrStep = 0, kAdrCheck = 1, kAdrInit = 2 };
 
-// value added back to a stored population (deviation storage only)
+// value added back to the stored population (s, i) of node m (half storage
+// only: w_i times the node's reference concentration)
 template <class P>
-__device__ __forceinline__ typename P::T adr_shift(const AdrArgs &a, int s, int i) {
+__device__ __forceinline__ typename P::T adr_ref(const AdrArgs &a, int s, int i,
+                                                 long long m) {
   using T = typename P::T;
-  return P::kDev ? Lattice<T>::w(i) * pick<T>(a.cref[s], a.fcref[s]) : T(0);
+  if constexpr (P::kDev)
+    return Lattice<T>::w(i) * T(a.rsrc[s * a.plane + m]);
+  else
+    return T(0);
+}
+// value removed before storing population i of a node whose reference is c
+template <class P>
+__device__ __forceinline__ typename P::T adr_unref(int i, typename P::T c) {
+  using T = typename P::T;
+  if constexpr (P::kDev)
+    return Lattice<T>::w(i) * c;
+  else
+    return T(0);
 }
 
 template <class P>
 __device__ __forceinline__ typename P::T adr_ld(const AdrArgs &a, int s, int i,
                                                 long long m) {
   const typename P::S *src = static_cast<const typename P::S *>(a.src);
-  return P::load(src[(long long)(s * 9 + i) * a.plane + m]) + adr_shift<P>(a, s, i);
+  return P::load(src[(long long)(s * 9 + i) * a.plane + m]) + adr_ref<P>(a, s, i, m);
 }
 
 // equilibrium factors E_i(u), shared by every species:
@@ -325,7 +334,8 @@ __device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
     const T c = adr_collide<P, NS>(a, s, lw, n, E, g, C);
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-      dst[(long long)(s * 9 + i) * plane + n] = P::store(g[i] - adr_shift<P>(a, s, i));
+      dst[(long long)(s * 9 + i) * plane + n] = P::store(g[i] - adr_unref<P>(i, c));
+    if constexpr (P::kDev) a.rdst[s * plane + n] = c;
     if (MODE == kAdrCheck) {
       T *cp = static_cast<T *>(a.cprev);
       acc[2 * s] += absT(c - cp[s * plane + n]);
@@ -352,9 +362,10 @@ __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-      g[s][i] = P::load(src[(long long)(s * 9 + i) * plane + n - (cy(i) * np + cx(i))]) +
-                adr_shift<P>(a, s, i);
+    for (int i = 0; i < 9; ++i) {
+      const long long m = n - (cy(i) * np + cx(i));
+      g[s][i] = P::load(src[(long long)(s * 9 + i) * plane + m]) + adr_ref<P>(a, s, i, m);
+    }
   }
   // the previous concentrations are loaded with the populations, so the
   // check step waits on memory once, like the plain step
@@ -375,7 +386,8 @@ __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
 #pragma unroll
     for (int i = 0; i < 9; ++i)
       dst[(long long)(s * 9 + i) * plane + n] =
-          P::store(g[s][i] + om * (c * E[i] - g[s][i]) - adr_shift<P>(a, s, i));
+          P::store(g[s][i] + om * (c * E[i] - g[s][i]) - adr_unref<P>(i, c));
+    if constexpr (P::kDev) a.rdst[s * plane + n] = c;
     if (MODE == kAdrCheck) {
       acc[2 * s] += absT(c - prev[s]);
       acc[2 * s + 1] += absT(c);
@@ -416,136 +428,20 @@ __global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
   }
 }
 
-// Bulk step: the interior formula for the nodes whose eight neighbours are
-// all fluid (link word 0); every other node is left to
-// adr_node_kernel<..., LIST = true>, launched right after.  VEC = 2 gives each thread
-// two nodes (x0 = 2t, x0 + 1): every plane is read with aligned two-wide
-// vector loads, the element a horizontal or diagonal pull needs from the
-// next pair over (x0 - 1 or x0 + 2) comes from the adjacent lane by a warp
-// shuffle, and only the first / last lane of a warp loads it itself.  Reads
-// outside the lattice rows or row ends are skipped, so all accesses stay in
-// bounds; their values only reach nodes the boundary kernel rewrites.
-template <class P, int NS, int MODE, int VEC>
+// Bulk step, one node per thread: the interior formula for the nodes whose
+// eight neighbours are all fluid (link word 0); every other node is left to
+// adr_node_kernel<..., LIST = true>, which runs beside it.
+template <class P, int NS, int MODE>
 __global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
     adr_bulk_kernel(const AdrArgs a) {
-  using S = typename P::S;
   using T = typename P::T;
-  const long long np = a.nx_pad, plane = a.plane;
-  const int y = blockIdx.y;
-  const S *__restrict__ src = static_cast<const S *>(a.src);
-  S *__restrict__ dst = static_cast<S *>(a.dst);
-  const T *__restrict__ U = static_cast<const T *>(a.u);
+  const int x = blockIdx.x * kBlockX + threadIdx.x;
+  const long long n = (long long)blockIdx.y * a.nx_pad + x;
+  const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
   T acc[2 * NS];
 #pragma unroll
   for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
-
-  if (VEC == 1) {
-    const int x = blockIdx.x * kBlockX + threadIdx.x;
-    const long long n = (long long)y * np + x;
-    const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
-    if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc);
-  } else {
-    using VS = typename Vec2<S>::type;
-    using VT = typename Vec2<T>::type;
-    const int lane = threadIdx.x & 31;
-    const int x0 = 2 * (blockIdx.x * kBlockX + threadIdx.x);
-    const bool valid = x0 < a.nx_pad;  // nx_pad is even: x0 + 1 is inside too
-    const long long n0 = (long long)y * np + x0;
-    uint2 lw = make_uint2(kSolidNode, kSolidNode);
-    if (valid) lw = *reinterpret_cast<const uint2 *>(a.links + n0);
-    const bool in0 = lw.x == 0u, in1 = lw.y == 0u;
-    // pulled values of both nodes, kept packed in the storage type until
-    // they are used (for half: one register per plane for two nodes)
-    VS pk[NS][9];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const int row = y - cy(i);
-        const bool rowok = valid && row >= 0 && row < a.ny;
-        const long long base = (long long)(s * 9 + i) * plane + (long long)row * np + x0;
-        S e0 = zero_of<S>(), e1 = zero_of<S>();
-        if (rowok) {
-          const VS v = *reinterpret_cast<const VS *>(src + base);
-          e0 = v.x;
-          e1 = v.y;
-        }
-        if (cx(i) == 0) {
-          pk[s][i] = pack2(e0, e1);
-        } else if (cx(i) > 0) {  // sources x0 - 1, x0
-          S left = __shfl_up_sync(0xffffffffu, e1, 1);
-          if (lane == 0) left = (rowok && x0 >= 1) ? src[base - 1] : zero_of<S>();
-          pk[s][i] = pack2(left, e0);
-        } else {  // sources x0 + 1, x0 + 2
-          S right = __shfl_down_sync(0xffffffffu, e0, 1);
-          if (lane == 31) right = (rowok && x0 + 2 < a.nx_pad) ? src[base + 2] : zero_of<S>();
-          pk[s][i] = pack2(e1, right);
-        }
-      }
-    }
-    T *__restrict__ cpb = static_cast<T *>(a.cprev) + n0;
-    T prev0[NS], prev1[NS];
-    if (MODE == kAdrCheck && valid) {
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        prev0[s] = cpb[s * plane];
-        prev1[s] = cpb[s * plane + 1];
-      }
-    }
-    if (valid && (in0 || in1)) {
-      const VT ux = *reinterpret_cast<const VT *>(U + n0);
-      const VT uy = *reinterpret_cast<const VT *>(U + plane + n0);
-      T E0[9], E1[9];
-      eq_factors<T>(ux.x, uy.x, E0);
-      eq_factors<T>(ux.y, uy.y, E1);
-#pragma unroll
-      for (int s = 0; s < NS; ++s) {
-        T g0[9], g1[9];
-        T c0 = T(0), c1 = T(0);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const T sh = adr_shift<P>(a, s, i);
-          g0[i] = P::load(pk[s][i].x) + sh;
-          g1[i] = P::load(pk[s][i].y) + sh;
-          c0 += g0[i];
-          c1 += g1[i];
-        }
-        const T om = pick<T>(a.omega[s], a.fomega[s]);
-        if (in0 && in1) {
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            const T sh = adr_shift<P>(a, s, i);
-            VS v;
-            v.x = P::store(g0[i] + om * (c0 * E0[i] - g0[i]) - sh);
-            v.y = P::store(g1[i] + om * (c1 * E1[i] - g1[i]) - sh);
-            *reinterpret_cast<VS *>(dst + (long long)(s * 9 + i) * plane + n0) = v;
-          }
-        } else {
-          // one interior node: scalar stores, the other node is not touched
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            const T sh = adr_shift<P>(a, s, i);
-            const long long o = (long long)(s * 9 + i) * plane + n0;
-            if (in0) dst[o] = P::store(g0[i] + om * (c0 * E0[i] - g0[i]) - sh);
-            if (in1) dst[o + 1] = P::store(g1[i] + om * (c1 * E1[i] - g1[i]) - sh);
-          }
-        }
-        if (MODE == kAdrCheck) {
-          if (in0) {
-            acc[2 * s] += absT(c0 - prev0[s]);
-            acc[2 * s + 1] += absT(c0);
-            cpb[s * plane] = c0;
-          }
-          if (in1) {
-            acc[2 * s] += absT(c1 - prev1[s]);
-            acc[2 * s + 1] += absT(c1);
-            cpb[s * plane + 1] = c1;
-          }
-        }
-      }
-    }
-  }
-
+  if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc);
   if (MODE == kAdrCheck) {
     const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
     block_sum_store<2 * NS, T>(acc, a.partials + b * (2 * NS));
@@ -556,12 +452,10 @@ __global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
 // out[s] = (1/ny) sum_y sum_i c_ix g*_{s,i}(xp, y).  One block.
 template <class P, int NS>
 __global__ void __launch_bounds__(kReduceThreads)
-    adr_flux_kernel(const void *g, const uint32_t *links, long long plane,
-                    int nx_pad, int ny, int xp, double cref0, double cref1,
-                    double cref2, double *out) {
+    adr_flux_kernel(const void *g, const float *ref, const uint32_t *links,
+                    long long plane, int nx_pad, int ny, int xp, double *out) {
   using S = typename P::S;
   const S *src = static_cast<const S *>(g);
-  const double cref[3] = {cref0, cref1, cref2};
   double acc[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) acc[s] = 0.0;
@@ -575,7 +469,7 @@ __global__ void __launch_bounds__(kReduceThreads)
       for (int i = 1; i < 9; ++i) {
         if (cx(i) == 0) continue;
         double gi = double(P::load(src[(long long)(s * 9 + i) * plane + n]));
-        if (P::kDev) gi += double(Lattice<float>::w(i)) * cref[s];
+        if (P::kDev) gi += double(Lattice<float>::w(i)) * double(ref[s * plane + n]);
         v += cx(i) > 0 ? gi : -gi;
       }
       acc[s] += v;
@@ -913,8 +807,8 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
 #ifndef LBM_ADR_SPLIT
 #define LBM_ADR_SPLIT 1
 #endif
-inline dim3 adr_bulk_grid(int vec, int nx_pad, int ny) {
-  const int per = vec * kBlockX;
+inline dim3 adr_bulk_grid(int nx_pad, int ny) {
+  const int per = kBlockX;
   return dim3(static_cast<unsigned>((nx_pad + per - 1) / per),
               static_cast<unsigned>(ny));
 }
@@ -926,12 +820,12 @@ inline long long adr_list_blocks(long long nbnd) {
   return (nbnd + kBlockX - 1) / kBlockX;
 }
 // partial-sum rows written by one check step
-inline long long adr_partial_rows(int vec, int nx_pad, int ny, long long nbnd) {
+inline long long adr_partial_rows(int nx_pad, int ny, long long nbnd) {
   if (!LBM_ADR_SPLIT) {
     const dim3 g = adr_node_grid(nx_pad, ny);
     return static_cast<long long>(g.x) * g.y;
   }
-  const dim3 g = adr_bulk_grid(vec, nx_pad, ny);
+  const dim3 g = adr_bulk_grid(nx_pad, ny);
   return static_cast<long long>(g.x) * g.y + adr_list_blocks(nbnd);
 }
 
@@ -945,9 +839,9 @@ template <class P>
 cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, cudaStream_t st,
                        const AdrOverlap *ov = nullptr);
 template <class P>
-cudaError_t launch_adr_flux(int ns, const void *g, const uint32_t *links,
-                            long long plane, int nx_pad, int ny, int xp,
-                            const double *cref, double *out, cudaStream_t st);
+cudaError_t launch_adr_flux(int ns, const void *g, const float *ref,
+                            const uint32_t *links, long long plane, int nx_pad,
+                            int ny, int xp, double *out, cudaStream_t st);
 template <class P>
 cudaError_t launch_flow(int mode, const FlowArgs &a, dim3 grid, cudaStream_t st);
 template <class P>

@@ -41,7 +41,7 @@ static void launch_bulk(const AdrArgs &a, dim3 bg, cudaStream_t st) {
     adr_tma_kernel<P, NS, MODE>
         <<<tma_grid<P, NS, MODE>(ntiles), kBlockX, L::kBytes, st>>>(a, a.status);
   } else {
-    adr_bulk_kernel<P, NS, MODE, P::kVec><<<bg, dim3(kBlockX), 0, st>>>(a);
+    adr_bulk_kernel<P, NS, MODE><<<bg, dim3(kBlockX), 0, st>>>(a);
   }
 }
 
@@ -63,7 +63,7 @@ static cudaError_t launch_adr_ns(int mode, const AdrArgs &a, cudaStream_t st,
           <<<adr_node_grid(a.nx_pad, a.ny), block, 0, st>>>(a);
     return cudaGetLastError();
   }
-  const dim3 bg = adr_bulk_grid(P::kVec, a.nx_pad, a.ny);
+  const dim3 bg = adr_bulk_grid(a.nx_pad, a.ny);
   AdrArgs b = a;
   b.part_off = static_cast<long long>(bg.x) * bg.y;
   const unsigned lb = static_cast<unsigned>(adr_list_blocks(a.nbnd));
@@ -105,19 +105,16 @@ cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, cudaStream_t st,
 }
 
 template <class P>
-cudaError_t launch_adr_flux(int ns, const void *g, const uint32_t *links,
-                            long long plane, int nx_pad, int ny, int xp,
-                            const double *cref, double *out, cudaStream_t st) {
+cudaError_t launch_adr_flux(int ns, const void *g, const float *ref,
+                            const uint32_t *links, long long plane, int nx_pad,
+                            int ny, int xp, double *out, cudaStream_t st) {
   const dim3 block(kReduceThreads);
   if (ns == 1)
-    adr_flux_kernel<P, 1><<<1, block, 0, st>>>(g, links, plane, nx_pad, ny, xp,
-                                               cref[0], cref[1], cref[2], out);
+    adr_flux_kernel<P, 1><<<1, block, 0, st>>>(g, ref, links, plane, nx_pad, ny, xp, out);
   else if (ns == 2)
-    adr_flux_kernel<P, 2><<<1, block, 0, st>>>(g, links, plane, nx_pad, ny, xp,
-                                               cref[0], cref[1], cref[2], out);
+    adr_flux_kernel<P, 2><<<1, block, 0, st>>>(g, ref, links, plane, nx_pad, ny, xp, out);
   else if (ns == 3)
-    adr_flux_kernel<P, 3><<<1, block, 0, st>>>(g, links, plane, nx_pad, ny, xp,
-                                               cref[0], cref[1], cref[2], out);
+    adr_flux_kernel<P, 3><<<1, block, 0, st>>>(g, ref, links, plane, nx_pad, ny, xp, out);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

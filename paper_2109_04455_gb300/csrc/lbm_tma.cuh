@@ -85,7 +85,12 @@ struct TmaLayout {
   static constexpr size_t kPop = sizeof(S) * kRow * kPlanes;     // bytes
   static constexpr size_t kU = sizeof(T) * kBlockX;              // one u row
   static constexpr size_t kLinks = sizeof(uint32_t) * kBlockX;
-  static constexpr size_t kStage = kPop + 2 * kU + kLinks;
+  // half storage: reference rows y-1, y, y+1 of every species (float,
+  // 16-byte margins)
+  static constexpr int kMR = 4;
+  static constexpr int kRefRow = kBlockX + 2 * kMR;
+  static constexpr size_t kRef = P::kDev ? sizeof(float) * kRefRow * 3 * NS : 0;
+  static constexpr size_t kStage = kPop + 2 * kU + kLinks + kRef;
   static constexpr size_t kBytes = 2 * kStage + 16;               // + 2 barriers
   static_assert(kPop % 16 == 0 && kU % 16 == 0, "16-byte aligned regions");
 };
@@ -115,50 +120,80 @@ __global__ void __launch_bounds__(kBlockX, 1)
   }
   __syncthreads();
 
-  // one thread: copies of tile t into stage st
+  // warp 0: copies of tile t into stage st, one copy per lane.  Copy q:
+  // q < planes: population plane q; then u_x, u_y, the link words; then
+  // (half storage) the 3 reference rows of every species.
+  constexpr int kCopies = L::kPlanes + 3 + (P::kDev ? 3 * NS : 0);
   auto issue = [&](long long t, int st) {
+    const int lane = threadIdx.x & 31;
     unsigned char *base = smem + st * L::kStage;
     const long long y = t / nxb;
     const long long x0 = (t % nxb) * kBlockX;
     const long long left = a.nx_pad - x0;              // multiple of 32
     const long long width = left < kBlockX ? left : kBlockX;
-    const long long plen = width + L::kM + (left > kBlockX ? L::kM : 0);
-    uint32_t bytes = 0;
-#pragma unroll 1
-    for (int p = 0; p < L::kPlanes; ++p) {
-      const int i = p % 9;
-      const long long start = p * plane + (y - cy(i)) * np + x0 - L::kM;
-      if (start >= 0 && start + plen <= total)
-        bytes += static_cast<uint32_t>(plen * sizeof(S));
-    }
-    bytes += static_cast<uint32_t>(width * (2 * sizeof(T) + sizeof(uint32_t)));
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&bars[st], bytes);
-#pragma unroll 1
-    for (int p = 0; p < L::kPlanes; ++p) {
-      const int i = p % 9;
-      const long long start = p * plane + (y - cy(i)) * np + x0 - L::kM;
-      if (start >= 0 && start + plen <= total)
-        bulk_g2s(base + static_cast<size_t>(p) * L::kRow * sizeof(S), src + start,
-                 static_cast<uint32_t>(plen * sizeof(S)), &bars[st]);
-    }
     const long long n0 = y * np + x0;
-    unsigned char *ub = base + L::kPop;
-    bulk_g2s(ub, U + n0, static_cast<uint32_t>(width * sizeof(T)), &bars[st]);
-    bulk_g2s(ub + L::kU, U + plane + n0, static_cast<uint32_t>(width * sizeof(T)),
-             &bars[st]);
-    bulk_g2s(ub + 2 * L::kU, a.links + n0,
-             static_cast<uint32_t>(width * sizeof(uint32_t)), &bars[st]);
+    // this lane's copies: destination, source, bytes (0 = not issued)
+    unsigned char *dq[2] = {nullptr, nullptr};
+    const void *sq[2] = {nullptr, nullptr};
+    uint32_t bq[2] = {0u, 0u};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      const int q = lane + 32 * r;
+      if (q >= kCopies) continue;
+      if (q < L::kPlanes) {
+        const int i = q % 9;
+        const long long plen = width + L::kM + (left > kBlockX ? L::kM : 0);
+        const long long start = q * plane + (y - cy(i)) * np + x0 - L::kM;
+        if (start >= 0 && start + plen <= total) {
+          dq[r] = base + static_cast<size_t>(q) * L::kRow * sizeof(S);
+          sq[r] = src + start;
+          bq[r] = static_cast<uint32_t>(plen * sizeof(S));
+        }
+      } else if (q < L::kPlanes + 3) {
+        const int j = q - L::kPlanes;   // 0: u_x, 1: u_y, 2: links
+        dq[r] = base + L::kPop + j * L::kU;
+        sq[r] = j < 2 ? static_cast<const void *>(U + j * plane + n0)
+                      : static_cast<const void *>(a.links + n0);
+        bq[r] = static_cast<uint32_t>(width * (j < 2 ? sizeof(T) : sizeof(uint32_t)));
+      } else {
+        const int qq = q - L::kPlanes - 3;   // species qq / 3, row y - 1 + qq % 3
+        long long rlen = width + L::kMR + (left > kBlockX ? L::kMR : 0);
+        long long start = (qq / 3) * plane + (y - 1 + qq % 3) * np + x0 - L::kMR;
+        long long skip = 0;
+        if (start < 0 && start + L::kMR >= 0) {
+          // first row of species 0: drop the left margin (only column 0, a
+          // boundary node, would read it)
+          skip = L::kMR;
+          start += skip;
+          rlen -= skip;
+        }
+        if (start >= 0 && start + rlen <= static_cast<long long>(NS) * plane) {
+          dq[r] = base + L::kPop + 2 * L::kU + L::kLinks +
+                  (static_cast<size_t>(qq) * L::kRefRow + skip) * sizeof(float);
+          sq[r] = a.rsrc + start;
+          bq[r] = static_cast<uint32_t>(rlen * sizeof(float));
+        }
+      }
+    }
+    const uint32_t bytes = __reduce_add_sync(0xffffffffu, bq[0] + bq[1]);
+    if (lane == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bars[st], bytes);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      if (bq[r]) bulk_g2s(dq[r], sq[r], bq[r], &bars[st]);
   };
 
   uint32_t phase[2] = {0u, 0u};
   long long t = blockIdx.x;
-  if (t < ntiles && threadIdx.x == 0) issue(t, 0);
+  if (t < ntiles && threadIdx.x < 32) issue(t, 0);
   int k = 0;
   for (; t < ntiles; t += gridDim.x, ++k) {
     const int st = k & 1;
     const long long tn = t + gridDim.x;
-    if (tn < ntiles && threadIdx.x == 0) issue(tn, st ^ 1);
+    if (tn < ntiles && threadIdx.x < 32) issue(tn, st ^ 1);
     if (!mbar_wait_bounded(&bars[st], phase[st])) s_abort = 1;
     __syncthreads();
     if (s_abort) {
@@ -175,6 +210,7 @@ __global__ void __launch_bounds__(kBlockX, 1)
     const S *rows = reinterpret_cast<const S *>(base);
     const T *su = reinterpret_cast<const T *>(base + L::kPop);
     const uint32_t *sl = reinterpret_cast<const uint32_t *>(base + L::kPop + 2 * L::kU);
+    const float *sr = reinterpret_cast<const float *>(base + L::kPop + 2 * L::kU + L::kLinks);
     const long long y = t / nxb;
     const int x = static_cast<int>((t % nxb) * kBlockX) + threadIdx.x;
     const long long n = y * np + x;
@@ -197,15 +233,18 @@ __global__ void __launch_bounds__(kBlockX, 1)
         T c = T(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-          g[i] = P::load(rows[(s * 9 + i) * L::kRow + L::kM + threadIdx.x - cx(i)]) +
-                 adr_shift<P>(a, s, i);
+          g[i] = P::load(rows[(s * 9 + i) * L::kRow + L::kM + threadIdx.x - cx(i)]);
+          if constexpr (P::kDev)   // reference of the source node x - c_i
+            g[i] += Lattice<T>::w(i) *
+                    sr[(s * 3 + 1 - cy(i)) * L::kRefRow + L::kMR + threadIdx.x - cx(i)];
           c += g[i];
         }
         const T om = pick<T>(a.omega[s], a.fomega[s]);
 #pragma unroll
         for (int i = 0; i < 9; ++i)
           dst[(long long)(s * 9 + i) * plane + n] =
-              P::store(g[i] + om * (c * E[i] - g[i]) - adr_shift<P>(a, s, i));
+              P::store(g[i] + om * (c * E[i] - g[i]) - adr_unref<P>(i, c));
+        if constexpr (P::kDev) a.rdst[s * plane + n] = c;
         if (MODE == kAdrCheck) {
           acc[2 * s] += absT(c - prev[s]);
           acc[2 * s + 1] += absT(c);
@@ -218,12 +257,14 @@ __global__ void __launch_bounds__(kBlockX, 1)
   }
 }
 
-// Whether a precision's bulk step uses the TMA-staged kernel.
+// Whether a precision's bulk step uses the TMA-staged kernel (see the
+// measurements in the design notes; the register-staged kernel is the
+// default).
 #ifndef LBM_ADR_TMA_F32
-#define LBM_ADR_TMA_F32 1
+#define LBM_ADR_TMA_F32 0
 #endif
 #ifndef LBM_ADR_TMA_F16
-#define LBM_ADR_TMA_F16 1
+#define LBM_ADR_TMA_F16 0
 #endif
 template <class P>
 constexpr bool adr_uses_tma() {
