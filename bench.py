@@ -145,8 +145,8 @@ def _peak_hbm():
 def _kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2109_04455_gb300", "csrc")
-    for f in ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "kernels_f32.cu",
-              "kernels_f16dev.cu", "kernels_f64.cu"):
+    for f in ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "lbm_tma.cuh",
+              "kernels_f32.cu", "kernels_f16dev.cu", "kernels_f64.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -194,7 +194,7 @@ def _algorithmic_bytes(geom, w, precision):
         ncat += int((((fl >> (4 * j)) & 0xF) == 3).sum())
     per_fluid = SPECIES * 9 * 2 * es + 2 * ue + 4
     if precision == "f16dev":
-        per_fluid += SPECIES * 2 * 4   # per-node reference, read + written
+        per_fluid += SPECIES * 2 * 2   # per-node half reference, read + written
     total = n_fluid * per_fluid + n_solid * 4 + ncat * 16
     return total, n_fluid, per_fluid
 

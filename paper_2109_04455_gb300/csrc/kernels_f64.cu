@@ -4,7 +4,7 @@
 namespace lbm {
 template cudaError_t launch_adr<PrecF64>(int, int, const AdrArgs &,
                                             cudaStream_t, const AdrOverlap *);
-template cudaError_t launch_adr_flux<PrecF64>(int, const void *, const float *,
+template cudaError_t launch_adr_flux<PrecF64>(int, const void *, const RefT *,
                                                  const uint32_t *, long long,
                                                  int, int, int, double *,
                                                  cudaStream_t);

@@ -305,7 +305,7 @@ struct lbm_adr_solver {
   double *partials = nullptr;
   double *scratch = nullptr;
   double *result = nullptr;
-  float *rbuf[2] = {nullptr, nullptr};  // reference concentrations (half)
+  RefT *rbuf[2] = {nullptr, nullptr};  // reference concentrations (half)
   int cur = 0;
   int64_t steps = 0;
   bool has_check = false;
@@ -330,7 +330,7 @@ static AdrLayout adr_layout(const lbm_geometry *g, const lbm_adr_params *p) {
   l.scratch = align256(kReduceGrid * 2 * ns * 8);
   l.result = align256(64 * 8);
   // half storage: per-node reference concentrations of both buffers
-  l.ref = p->precision == LBM_F16DEV ? align256(ns * pl * 4) : 0;
+  l.ref = p->precision == LBM_F16DEV ? align256(ns * pl * sizeof(RefT)) : 0;
   l.total = 2 * l.buf + l.cprev + l.partials + l.scratch + l.result + 2 * l.ref;
   return l;
 }
@@ -362,7 +362,7 @@ static cudaError_t adr_flux_launch(const lbm_adr_solver *s, cudaStream_t st) {
   const lbm_geometry *g = s->g;
   int xp = s->p.x_plane < 0 ? g->nx - 3 : s->p.x_plane;
   const void *cur = s->buf[s->cur];
-  const float *ref = s->rbuf[s->cur];
+  const RefT *ref = s->rbuf[s->cur];
   double *out = s->result + 8;
   const int ns = s->p.nspecies;
   switch (s->p.precision) {
@@ -432,8 +432,8 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
                                          l.scratch);
   if (l.ref) {
     char *rb = b + 2 * l.buf + l.cprev + l.partials + l.scratch + l.result;
-    s->rbuf[0] = reinterpret_cast<float *>(rb);
-    s->rbuf[1] = reinterpret_cast<float *>(rb + l.ref);
+    s->rbuf[0] = reinterpret_cast<RefT *>(rb);
+    s->rbuf[1] = reinterpret_cast<RefT *>(rb + l.ref);
   }
   s->nb = adr_partial_rows(g->nx_pad, g->ny,
                            static_cast<long long>(g->bnodes.size()));
@@ -887,7 +887,7 @@ static double *g_addr[256] = {};  // device address of the array, per device
 // all three slots, so nothing has to start at zero.
 template <class P, int NS>
 __global__ void __launch_bounds__(kRowsPerBlock)
-    outflux_partial_noalloc_kernel(const void *g, const float *ref,
+    outflux_partial_noalloc_kernel(const void *g, const RefT *ref,
                                    const uint32_t *links, long long plane,
                                    int nx_pad, int ny, int xp, double *part) {
   using S = typename P::S;
@@ -903,7 +903,7 @@ __global__ void __launch_bounds__(kRowsPerBlock)
         for (int i = 1; i < 9; ++i) {
           if (cx(i) == 0) continue;
           double gi = double(P::load(src[(long long)(s * 9 + i) * plane + n]));
-          if (P::kDev) gi += double(Lattice<float>::w(i)) * double(ref[s * plane + n]);
+          if (P::kDev) gi += double(Lattice<float>::w(i)) * double(ref_get(ref, s * plane + n));
           acc[s] += cx(i) > 0 ? gi : -gi;
         }
       }
@@ -927,7 +927,7 @@ __global__ void __launch_bounds__(kReduceThreads)
 }
 
 template <class P>
-cudaError_t outflux_noalloc_launch(int ns, const void *g, const float *ref,
+cudaError_t outflux_noalloc_launch(int ns, const void *g, const RefT *ref,
                                    const uint32_t *links, long long plane,
                                    int nx_pad, int ny, int xp, double *scratch,
                                    cudaStream_t st) {

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kReduceThreads)
       for (int i = 1; i < 9; ++i) {
         if (cx(i) == 0) continue;
         double gi = double(P::load(src[(long long)(s * 9 + i) * a.plane + n]));
-        if (P::kDev) gi += double(Lattice<float>::w(i)) * double(a.rdst[s * a.plane + n]);
+        if (P::kDev) gi += double(Lattice<float>::w(i)) * double(ref_get(a.rdst, s * a.plane + n));
         v += cx(i) > 0 ? gi : -gi;
       }
       acc[s] += v;
@@ -268,7 +268,7 @@ BatchLayout batch_layout(int count, const lbm_geometry *const *geoms,
     const size_t pl = static_cast<size_t>(geoms[i]->nx_pad) * geoms[i]->ny;
     const size_t b = a256(ns * 9 * pl * store_b(p[0].precision));
     const size_t c = a256(ns * pl * comp_b(p[0].precision));
-    const size_t r = p[0].precision == LBM_F16DEV ? a256(ns * pl * 4) : 0;
+    const size_t r = p[0].precision == LBM_F16DEV ? a256(ns * pl * sizeof(RefT)) : 0;
     l.inst_off.push_back(off);
     l.buf.push_back(b);
     l.cprev.push_back(c);
@@ -404,7 +404,7 @@ lbm_status init_states(lbm_batch *b, cudaStream_t st) {
       a.src = nullptr;
       a.dst = const_cast<void *>(b->table[2 * i].src);  // initial state: buffer 0
       a.rsrc = nullptr;
-      a.rdst = const_cast<float *>(b->table[2 * i].rsrc);
+      a.rdst = const_cast<RefT *>(b->table[2 * i].rsrc);
       switch (b->prec) {
         case LBM_F64: e = launch_adr<PrecF64>(b->ns, kAdrInit, a, st); break;
         case LBM_F32: e = launch_adr<PrecF32>(b->ns, kAdrInit, a, st); break;
@@ -510,11 +510,11 @@ extern "C" lbm_status lbm_batch_create(int32_t count,
       a.fomega[k] = static_cast<float>(a.omega[k]);
       a.fcin[k] = static_cast<float>(a.cin[k]);
     }
-    float *ref0 = nullptr, *ref1 = nullptr;
+    RefT *ref0 = nullptr, *ref1 = nullptr;
     if (l.ref[i]) {
       char *rb = base + l.inst_off[i] + 2 * l.buf[i] + l.cprev[i];
-      ref0 = reinterpret_cast<float *>(rb);
-      ref1 = reinterpret_cast<float *>(rb + l.ref[i]);
+      ref0 = reinterpret_cast<RefT *>(rb);
+      ref1 = reinterpret_cast<RefT *>(rb + l.ref[i]);
     }
     a.src = buf0;
     a.dst = buf1;

@@ -60,7 +60,7 @@ struct PrecF32 {
   static __device__ __forceinline__ S store(T v) { return v; }
 };
 // half storage of the deviation g - w_i R from a per-node reference R (the
-// node's concentration when the value was stored, kept in float beside the
+// node's concentration when the value was stored, kept in half beside the
 // populations), scaled by 2^14 (exact) so that the deviations of dilute
 // species stay in half's normal range (|value| <= 0.45 * 2^14 < 65504);
 // rounded to nearest even.  The deviation is the advective and
@@ -143,6 +143,17 @@ template <>
 __device__ __forceinline__ __half zero_of<__half>() { return __float2half_rn(0.0f); }
 
 
+// Reference concentrations of the half path are themselves stored in half:
+// any reference works as long as the writer and every reader use the same
+// value, so the writer subtracts the rounded reference it stores.
+using RefT = __half;
+__device__ __forceinline__ float ref_get(const RefT *r, long long k) {
+  return __half2float(r[k]);
+}
+__device__ __forceinline__ float ref_round(float c) {
+  return __half2float(__float2half_rn(c));
+}
+
 // Kernel parameters come in double and in float; the float paths read the
 // float copy, so no thread converts a double (this part's FP64 pipe is
 // narrow enough for per-thread conversions to show up in a step's time).
@@ -180,8 +191,8 @@ struct AdrArgs {
   float fomega[3], fcin[3]; // the same in float
   // half storage: reference concentrations [ns][plane] of the src and dst
   // populations (the stored value is g - w_i R of its node)
-  const float *rsrc;
-  float *rdst;
+  const RefT *rsrc;
+  RefT *rdst;
 };
 
 enum AdrMode { kAdrStep = 0, kAdrCheck = 1, kAdrInit = 2 };
@@ -193,7 +204,7 @@ __device__ __forceinline__ typename P::T adr_ref(const AdrArgs &a, int s, int i,
                                                  long long m) {
   using T = typename P::T;
   if constexpr (P::kDev)
-    return Lattice<T>::w(i) * T(a.rsrc[s * a.plane + m]);
+    return Lattice<T>::w(i) * T(ref_get(a.rsrc, s * a.plane + m));
   else
     return T(0);
 }
@@ -332,10 +343,14 @@ __device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
       if (lw != 0u) adr_boundary<P>(a, s, lw, n, x, g);
     }
     const T c = adr_collide<P, NS>(a, s, lw, n, E, g, C);
+    T cq = c;   // the reference stored with the populations (half path)
+    if constexpr (P::kDev) {
+      cq = ref_round(c);
+      a.rdst[s * plane + n] = __float2half_rn(c);
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-      dst[(long long)(s * 9 + i) * plane + n] = P::store(g[i] - adr_unref<P>(i, c));
-    if constexpr (P::kDev) a.rdst[s * plane + n] = c;
+      dst[(long long)(s * 9 + i) * plane + n] = P::store(g[i] - adr_unref<P>(i, cq));
     if (MODE == kAdrCheck) {
       T *cp = static_cast<T *>(a.cprev);
       acc[2 * s] += absT(c - cp[s * plane + n]);
@@ -349,9 +364,13 @@ __device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
 // interior formula (pull from x - c_i, BGK, no source).  All populations of
 // all species are loaded before any arithmetic, so a thread keeps NS*9
 // independent loads in flight.
+// rn (half storage only, optional): the reference concentrations of the
+// 3 x 3 neighbourhood, rn[s][1 - c_iy][1 - c_ix] for the source of direction
+// i; without it they are loaded here.
 template <class P, int NS, int MODE>
 __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
-                                                  typename P::T (&acc)[2 * NS]) {
+                                                  typename P::T (&acc)[2 * NS],
+                                                  const float (*rn)[3][3] = nullptr) {
   using S = typename P::S;
   using T = typename P::T;
   const long long np = a.nx_pad, plane = a.plane;
@@ -364,7 +383,10 @@ __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const long long m = n - (cy(i) * np + cx(i));
-      g[s][i] = P::load(src[(long long)(s * 9 + i) * plane + m]) + adr_ref<P>(a, s, i, m);
+      g[s][i] = P::load(src[(long long)(s * 9 + i) * plane + m]);
+      if constexpr (P::kDev)
+        g[s][i] += rn ? Lattice<T>::w(i) * T(rn[s][1 - cy(i)][1 - cx(i)])
+                      : adr_ref<P>(a, s, i, m);
     }
   }
   // the previous concentrations are loaded with the populations, so the
@@ -383,11 +405,15 @@ __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
 #pragma unroll
     for (int i = 0; i < 9; ++i) c += g[s][i];
     const T om = pick<T>(a.omega[s], a.fomega[s]);
+    T cq = c;   // the reference stored with the populations (half path)
+    if constexpr (P::kDev) {
+      cq = ref_round(c);
+      a.rdst[s * plane + n] = __float2half_rn(c);
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i)
       dst[(long long)(s * 9 + i) * plane + n] =
-          P::store(g[s][i] + om * (c * E[i] - g[s][i]) - adr_unref<P>(i, c));
-    if constexpr (P::kDev) a.rdst[s * plane + n] = c;
+          P::store(g[s][i] + om * (c * E[i] - g[s][i]) - adr_unref<P>(i, cq));
     if (MODE == kAdrCheck) {
       acc[2 * s] += absT(c - prev[s]);
       acc[2 * s + 1] += absT(c);
@@ -441,7 +467,38 @@ __global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
   T acc[2 * NS];
 #pragma unroll
   for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
-  if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc);
+  if constexpr (P::kDev) {
+    // Reference concentrations of the 3 x 3 neighbourhood: every lane loads
+    // its own column of rows y-1, y, y+1; columns x-1 and x+1 come from the
+    // adjacent lanes (the first / last lane of a warp loads its outer one).
+    // 3 loads and 6 shuffles per species instead of 9 loads.
+    const int lane = threadIdx.x & 31;
+    const int y = blockIdx.y;
+    const long long np = a.nx_pad;
+    const bool inx = x < a.nx_pad;
+    float rn[NS][3][3];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int row = y - 1 + k;
+        const bool ok = inx && row >= 0 && row < a.ny;
+        const RefT *rr = a.rsrc + s * a.plane + (long long)row * np;
+        const float v = ok ? ref_get(rr, x) : 0.0f;
+        float left = __shfl_up_sync(0xffffffffu, v, 1);
+        float right = __shfl_down_sync(0xffffffffu, v, 1);
+        if (lane == 0) left = (ok && x >= 1) ? ref_get(rr, x - 1) : 0.0f;
+        if (lane == 31) right = (ok && x + 1 < a.nx_pad) ? ref_get(rr, x + 1) : 0.0f;
+        // index 1 - c_ix: column x - c_ix, the source of direction i
+        rn[s][k][0] = left;    // column x - 1 (c_ix = +1)
+        rn[s][k][1] = v;       // column x     (c_ix =  0)
+        rn[s][k][2] = right;   // column x + 1 (c_ix = -1)
+      }
+    }
+    if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc, rn);
+  } else {
+    if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc);
+  }
   if (MODE == kAdrCheck) {
     const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
     block_sum_store<2 * NS, T>(acc, a.partials + b * (2 * NS));
@@ -452,7 +509,7 @@ __global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
 // out[s] = (1/ny) sum_y sum_i c_ix g*_{s,i}(xp, y).  One block.
 template <class P, int NS>
 __global__ void __launch_bounds__(kReduceThreads)
-    adr_flux_kernel(const void *g, const float *ref, const uint32_t *links,
+    adr_flux_kernel(const void *g, const RefT *ref, const uint32_t *links,
                     long long plane, int nx_pad, int ny, int xp, double *out) {
   using S = typename P::S;
   const S *src = static_cast<const S *>(g);
@@ -469,7 +526,7 @@ __global__ void __launch_bounds__(kReduceThreads)
       for (int i = 1; i < 9; ++i) {
         if (cx(i) == 0) continue;
         double gi = double(P::load(src[(long long)(s * 9 + i) * plane + n]));
-        if (P::kDev) gi += double(Lattice<float>::w(i)) * double(ref[s * plane + n]);
+        if (P::kDev) gi += double(Lattice<float>::w(i)) * double(ref_get(ref, s * plane + n));
         v += cx(i) > 0 ? gi : -gi;
       }
       acc[s] += v;
@@ -839,7 +896,7 @@ template <class P>
 cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, cudaStream_t st,
                        const AdrOverlap *ov = nullptr);
 template <class P>
-cudaError_t launch_adr_flux(int ns, const void *g, const float *ref,
+cudaError_t launch_adr_flux(int ns, const void *g, const RefT *ref,
                             const uint32_t *links, long long plane, int nx_pad,
                             int ny, int xp, double *out, cudaStream_t st);
 template <class P>

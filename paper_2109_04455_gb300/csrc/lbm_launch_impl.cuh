@@ -105,7 +105,7 @@ cudaError_t launch_adr(int ns, int mode, const AdrArgs &a, cudaStream_t st,
 }
 
 template <class P>
-cudaError_t launch_adr_flux(int ns, const void *g, const float *ref,
+cudaError_t launch_adr_flux(int ns, const void *g, const RefT *ref,
                             const uint32_t *links, long long plane, int nx_pad,
                             int ny, int xp, double *out, cudaStream_t st) {
   const dim3 block(kReduceThreads);

@@ -85,11 +85,11 @@ struct TmaLayout {
   static constexpr size_t kPop = sizeof(S) * kRow * kPlanes;     // bytes
   static constexpr size_t kU = sizeof(T) * kBlockX;              // one u row
   static constexpr size_t kLinks = sizeof(uint32_t) * kBlockX;
-  // half storage: reference rows y-1, y, y+1 of every species (float,
-  // 16-byte margins)
-  static constexpr int kMR = 4;
+  // half storage: reference rows y-1, y, y+1 of every species (16-byte
+  // margins)
+  static constexpr int kMR = 16 / static_cast<int>(sizeof(RefT));
   static constexpr int kRefRow = kBlockX + 2 * kMR;
-  static constexpr size_t kRef = P::kDev ? sizeof(float) * kRefRow * 3 * NS : 0;
+  static constexpr size_t kRef = P::kDev ? sizeof(RefT) * kRefRow * 3 * NS : 0;
   static constexpr size_t kStage = kPop + 2 * kU + kLinks + kRef;
   static constexpr size_t kBytes = 2 * kStage + 16;               // + 2 barriers
   static_assert(kPop % 16 == 0 && kU % 16 == 0, "16-byte aligned regions");
@@ -169,9 +169,9 @@ __global__ void __launch_bounds__(kBlockX, 1)
         }
         if (start >= 0 && start + rlen <= static_cast<long long>(NS) * plane) {
           dq[r] = base + L::kPop + 2 * L::kU + L::kLinks +
-                  (static_cast<size_t>(qq) * L::kRefRow + skip) * sizeof(float);
+                  (static_cast<size_t>(qq) * L::kRefRow + skip) * sizeof(RefT);
           sq[r] = a.rsrc + start;
-          bq[r] = static_cast<uint32_t>(rlen * sizeof(float));
+          bq[r] = static_cast<uint32_t>(rlen * sizeof(RefT));
         }
       }
     }
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kBlockX, 1)
     const S *rows = reinterpret_cast<const S *>(base);
     const T *su = reinterpret_cast<const T *>(base + L::kPop);
     const uint32_t *sl = reinterpret_cast<const uint32_t *>(base + L::kPop + 2 * L::kU);
-    const float *sr = reinterpret_cast<const float *>(base + L::kPop + 2 * L::kU + L::kLinks);
+    const RefT *sr = reinterpret_cast<const RefT *>(base + L::kPop + 2 * L::kU + L::kLinks);
     const long long y = t / nxb;
     const int x = static_cast<int>((t % nxb) * kBlockX) + threadIdx.x;
     const long long n = y * np + x;
@@ -236,15 +236,19 @@ __global__ void __launch_bounds__(kBlockX, 1)
           g[i] = P::load(rows[(s * 9 + i) * L::kRow + L::kM + threadIdx.x - cx(i)]);
           if constexpr (P::kDev)   // reference of the source node x - c_i
             g[i] += Lattice<T>::w(i) *
-                    sr[(s * 3 + 1 - cy(i)) * L::kRefRow + L::kMR + threadIdx.x - cx(i)];
+                    __half2float(sr[(s * 3 + 1 - cy(i)) * L::kRefRow + L::kMR + threadIdx.x - cx(i)]);
           c += g[i];
         }
         const T om = pick<T>(a.omega[s], a.fomega[s]);
+        T cq = c;
+        if constexpr (P::kDev) {
+          cq = ref_round(c);
+          a.rdst[s * plane + n] = __float2half_rn(c);
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i)
           dst[(long long)(s * 9 + i) * plane + n] =
-              P::store(g[i] + om * (c * E[i] - g[i]) - adr_unref<P>(i, c));
-        if constexpr (P::kDev) a.rdst[s * plane + n] = c;
+              P::store(g[i] + om * (c * E[i] - g[i]) - adr_unref<P>(i, cq));
         if (MODE == kAdrCheck) {
           acc[2 * s] += absT(c - prev[s]);
           acc[2 * s + 1] += absT(c);
