@@ -364,13 +364,9 @@ __device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
 // interior formula (pull from x - c_i, BGK, no source).  All populations of
 // all species are loaded before any arithmetic, so a thread keeps NS*9
 // independent loads in flight.
-// rn (half storage only, optional): the reference concentrations of the
-// 3 x 3 neighbourhood, rn[s][1 - c_iy][1 - c_ix] for the source of direction
-// i; without it they are loaded here.
 template <class P, int NS, int MODE>
 __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
-                                                  typename P::T (&acc)[2 * NS],
-                                                  const float (*rn)[3][3] = nullptr) {
+                                                  typename P::T (&acc)[2 * NS]) {
   using S = typename P::S;
   using T = typename P::T;
   const long long np = a.nx_pad, plane = a.plane;
@@ -383,10 +379,7 @@ __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const long long m = n - (cy(i) * np + cx(i));
-      g[s][i] = P::load(src[(long long)(s * 9 + i) * plane + m]);
-      if constexpr (P::kDev)
-        g[s][i] += rn ? Lattice<T>::w(i) * T(rn[s][1 - cy(i)][1 - cx(i)])
-                      : adr_ref<P>(a, s, i, m);
+      g[s][i] = P::load(src[(long long)(s * 9 + i) * plane + m]) + adr_ref<P>(a, s, i, m);
     }
   }
   // the previous concentrations are loaded with the populations, so the
@@ -467,38 +460,10 @@ __global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
   T acc[2 * NS];
 #pragma unroll
   for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
-  if constexpr (P::kDev) {
-    // Reference concentrations of the 3 x 3 neighbourhood: every lane loads
-    // its own column of rows y-1, y, y+1; columns x-1 and x+1 come from the
-    // adjacent lanes (the first / last lane of a warp loads its outer one).
-    // 3 loads and 6 shuffles per species instead of 9 loads.
-    const int lane = threadIdx.x & 31;
-    const int y = blockIdx.y;
-    const long long np = a.nx_pad;
-    const bool inx = x < a.nx_pad;
-    float rn[NS][3][3];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int row = y - 1 + k;
-        const bool ok = inx && row >= 0 && row < a.ny;
-        const RefT *rr = a.rsrc + s * a.plane + (long long)row * np;
-        const float v = ok ? ref_get(rr, x) : 0.0f;
-        float left = __shfl_up_sync(0xffffffffu, v, 1);
-        float right = __shfl_down_sync(0xffffffffu, v, 1);
-        if (lane == 0) left = (ok && x >= 1) ? ref_get(rr, x - 1) : 0.0f;
-        if (lane == 31) right = (ok && x + 1 < a.nx_pad) ? ref_get(rr, x + 1) : 0.0f;
-        // index 1 - c_ix: column x - c_ix, the source of direction i
-        rn[s][k][0] = left;    // column x - 1 (c_ix = +1)
-        rn[s][k][1] = v;       // column x     (c_ix =  0)
-        rn[s][k][2] = right;   // column x + 1 (c_ix = -1)
-      }
-    }
-    if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc, rn);
-  } else {
-    if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc);
-  }
+  // (half storage: the references of the nine source nodes are read next
+  // to the populations; gathering them with warp shuffles instead measured
+  // slower, the shuffles keep the population loads from being issued early)
+  if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc);
   if (MODE == kAdrCheck) {
     const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
     block_sum_store<2 * NS, T>(acc, a.partials + b * (2 * NS));

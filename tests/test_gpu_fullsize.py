@@ -91,3 +91,30 @@ def test_full_size_no_catalyst_no_product(big):
     c, info = lbm.lbm_adr_solve(g0, prm, u64.float())
     assert torch.count_nonzero(c[1:]).item() == 0
     assert info["flux"][1] == 0.0 and info["flux"][2] == 0.0
+
+
+def test_cascade_steady_state_precisions():
+    """Two-membrane cascade lattice (2048 x 512, 80 fibers, Pe = 10) solved to
+    steady state: FP64 to a per-step residual of 1e-9, FP32 and FP16-deviation
+    storage to 1e-6, on the same converged FP64 flow.  Steady efficiencies
+    agree within 1e-4 (FP32) and 1e-3 (FP16)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    w = inputs.two_membrane_cascade(seed=0, pe=10.0)
+    geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
+    u64, finfo = lbm.lbm_flow_solve(geom, w.tau_flow, w.u0, 400000, tol=1e-9,
+                                    check_every=1000, precision=lbm.LBM_F64)
+    assert finfo["converged"]
+    eps = {}
+    for prec, tol in ((lbm.LBM_F64, 1e-9), (lbm.LBM_F32, 1e-6),
+                      (lbm.LBM_F16DEV, 1e-6)):
+        u = u64 if prec == lbm.LBM_F64 else u64.float()
+        prm = lbm.adr_params(3, w.tau_c, precision=prec, max_steps=400000,
+                             tol=tol, check_every=1000)
+        _, info = lbm.lbm_adr_solve(geom, prm, u, want_conc=False)
+        if prec == lbm.LBM_F64:
+            assert info["converged"]
+        eps[prec] = info["eps"]
+    assert eps[lbm.LBM_F64] > 1e-3
+    assert abs(eps[lbm.LBM_F32] - eps[lbm.LBM_F64]) < 1e-4
+    assert abs(eps[lbm.LBM_F16DEV] - eps[lbm.LBM_F64]) < 1e-3
