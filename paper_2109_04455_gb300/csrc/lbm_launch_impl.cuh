@@ -40,9 +40,12 @@ static void launch_bulk(const AdrArgs &a, dim3 bg, cudaStream_t st) {
     const long long ntiles = static_cast<long long>(bg.x) * bg.y;
     adr_tma_kernel<P, NS, MODE>
         <<<tma_grid<P, NS, MODE>(ntiles), kBlockX, L::kBytes, st>>>(a, a.status);
-  } else {
-    adr_bulk_kernel<P, NS, MODE><<<bg, dim3(kBlockX), 0, st>>>(a);
+    return;
   }
+  if constexpr (P::kDev && LBM_ADR_PAIR_F16)
+    adr_bulk_pair_kernel<NS, MODE><<<bg, dim3(kPairThreads), 0, st>>>(a);
+  else
+    adr_bulk_kernel<P, NS, MODE><<<bg, dim3(kBlockX), 0, st>>>(a);
 }
 
 template <class P, int NS>
