@@ -50,10 +50,17 @@ def _args():
     ap.add_argument("--ny", type=int, default=4096)
     ap.add_argument("--fibers-per-band", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "sweep"],
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "sweep", "adjoint", "series"],
                     help="large: the 67M-node membrane (default line); "
                          "sweep: the 64-instance Pe x Da sweep, batched "
-                         "FP32 / FP16 against unbatched FP64 (solves/s)")
+                         "FP32 / FP16 against unbatched FP64 (solves/s); "
+                         "adjoint: discrete-adjoint iterations on the "
+                         "67M-node membrane (f32 or f64); series: the "
+                         "paper's 2D experiment series (isolated fiber, "
+                         "fiber pairs, side-by-side fiber against Pe), "
+                         "batched, to steady state")
+    ap.add_argument("--adjoint-iters", type=int, default=200)
     ap.add_argument("--sweep-instances", type=int, default=64)
     ap.add_argument("--sweep-max-steps", type=int, default=5000)
     ap.add_argument("--sweep-flow-steps", type=int, default=3000)
@@ -142,11 +149,21 @@ def _peak_hbm():
         return 6800.0, "fallback"
 
 
-def _kernel_source_hash():
+KERNEL_SOURCES = {
+    "f32": ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "lbm_tma.cuh",
+            "kernels_f32.cu"),
+    "f16dev": ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "lbm_tma.cuh",
+               "lbm_f16.cuh", "kernels_f16dev.cu"),
+    "f64": ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "lbm_tma.cuh",
+            "kernels_f64.cu"),
+}
+
+
+def _kernel_source_hash(precision: str):
+    """Hash of the sources the precision's step kernel is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2109_04455_gb300", "csrc")
-    for f in ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "lbm_tma.cuh",
-              "kernels_f32.cu", "kernels_f16dev.cu", "kernels_f64.cu"):
+    for f in KERNEL_SOURCES[precision]:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -166,7 +183,7 @@ def _ncu_traffic(precision: str, units_per_launch: int):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
     try:
-        if kv.get("kernel_source_hash") != _kernel_source_hash():
+        if kv.get("kernel_source_hash") != _kernel_source_hash(precision):
             return None
         per_unit = float(kv["dram_bytes_per_fluid_node"])
         return per_unit * units_per_launch
@@ -421,7 +438,9 @@ def run_gpu(a):
                          "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic,
                          "peak_kind": f"{peak_kind} (copy bandwidth)",
-                         "kernel": f"adr_kernel<{a.precision},3 species,step>",
+                         "kernel": ("adr_bulk_pair_kernel<3 species,step> "
+                                    "(f16dev)" if a.precision == "f16dev" else
+                                    f"adr_bulk_kernel<{a.precision},3 species,step>"),
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "bytes_per_fluid_node": per_fluid,
                          "fluid_nodes": n_fluid,
@@ -517,12 +536,133 @@ def run_sweep(a):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# discrete adjoint on the large lattice
+# ---------------------------------------------------------------------------
+def run_adjoint(a):
+    """Adjoint iterations nu <- K^T (P^T nu + l) on the large membrane.
+    Untimed: flow, and a few hundred forward steps (the adjoint linearises
+    around the forward's last checked state).  Timed with CUDA events:
+    lbm_adr_adjoint with a fixed iteration count (tol = 0), which also
+    zeroes its outputs and runs the rate-gradient kernel once at the end.
+    Reports adjoint species MLUPS of whole calls of 2N iterations, and the
+    HBM roofline of one adjoint iteration (time of a 2N-iteration call less
+    that of an N-iteration call, over N), whose algorithmic bytes per fluid
+    node equal the forward step's (the gather of 27 values, 27 stores, u
+    and the link word)."""
+    import torch
+
+    from paper_2109_04455_gb300 import lbm
+    torch.cuda.set_device(0)
+    if a.precision == "f16dev":
+        raise SystemExit("the adjoint runs in f32 or f64")
+    prec = lbm.PRECISIONS[a.precision]
+    w = _workload(a)
+    geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
+    u, _ = lbm.lbm_flow_solve(geom, w.tau_flow, w.u0, a.flow_steps,
+                              precision=lbm.LBM_F64 if prec == lbm.LBM_F64
+                              else lbm.LBM_F32)
+    prm = lbm.adr_params(SPECIES, w.tau_c, w.c_in, precision=prec)
+    sv = lbm.ADRSolver(geom, prm, u).init()
+    sv.run(CHUNK - 2, check=False)
+    sv.run(2)
+    nfib = w.fibers.shape[0]
+    n_it = max(2, a.adjoint_iters)
+    for _ in range(max(1, a.warmup)):
+        sv.adjoint(20, tol=0.0, check_every=20, nfibers=nfib)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+        enable_timing=True)
+
+    def timed(n):
+        ev0.record()
+        out = sv.adjoint(n, tol=0.0, check_every=n, nfibers=nfib)
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) * 1e-3, out
+
+    t1s, t2s = [], []
+    with ClockSampler(0) as clk:
+        for _ in range(a.steps):
+            t1s.append(timed(n_it)[0])
+            t2, (_, _, dw, info) = timed(2 * n_it)
+            t2s.append(t2)
+    t = sum(t2s) / len(t2s)
+    alg_bytes, n_fluid, per_fluid = _algorithmic_bytes(geom, w, a.precision)
+    # per iteration: the difference of the two call lengths, free of the
+    # fixed per-call work (workspace zeroing, fiber-id upload, gradients)
+    per_it = (t - sum(t1s) / len(t1s)) / n_it
+    n_it = 2 * n_it
+    achieved = alg_bytes / per_it / 1e9
+    peak, peak_kind = _peak_hbm()
+    line = {"metric": "adjoint species MLUPS (ADR, 3 species)",
+            "value": SPECIES * w.nx * w.ny * n_it / t / 1e6, "unit": UNIT,
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True,
+            "dtype": a.precision, "data": "synthetic (seeded fiber geometry)",
+            "config": dict(_config(a, w), adjoint_iters_per_step=n_it),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "peak_kind": f"{peak_kind} (copy bandwidth)",
+                         "kernel": f"adj_kernel<{a.precision},3 species>",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "bytes_per_fluid_node": per_fluid,
+                         "avg_iteration_ms": per_it * 1e3},
+            "clocks": clk.summary(),
+            "eps": info["eps"],
+            "dw_abs_max": float(dw.abs().max().item())}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the paper's 2D experiment series
+# ---------------------------------------------------------------------------
+def run_series(a):
+    """Isolated A->B fiber (Da = 150, 1.5), A->B->C fiber pairs at xi = 2,
+    20, 100 and the side-by-side fiber (Da = 150), Pe = 2..100: 48 lattices
+    of 300x300 and 1000x300.  Untimed: one FP64 flow per geometry.  Timed
+    on the host clock (the solves end synchronised): the launch-shape tuning
+    and the batched ADR solves (two batches, 2 and 3 species) to a per-step
+    residual of 1e-7 or the 300000-step cap.  Reports solves/s, and per lattice the efficiency, the
+    collision-zone model's value and the production rate."""
+    import torch
+
+    from paper_2109_04455_gb300 import lbm, series
+    torch.cuda.set_device(0)
+    prec = lbm.PRECISIONS[a.precision]
+    items = series.workloads()
+    flows = series.solve_flows(items)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rows, shapes = series.run(items, flows, precision=prec, tol=1e-7,
+                              max_steps=300000)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out = {"metric": "paper 2D series solves/s (ADR to steady state)",
+           "value": len(rows) / t, "unit": "solves/s",
+           "higher_is_better": True, "seconds": t, "dtype": a.precision,
+           "lattices": len(rows),
+           "nodes": sum(r["nx"] * r["ny"] for r in rows),
+           "converged": sum(r["converged"] for r in rows),
+           "steps": sum(r["steps"] for r in rows),
+           "launch_shapes": shapes,
+           "timing": "host clock around the batched solves, tuning included",
+           "rows": [{k: (round(v, 8) if isinstance(v, float) else v)
+                     for k, v in r.items() if k != "flux"} for r in rows]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "sweep":
         run_sweep(a)
+    elif a.workload == "adjoint":
+        run_adjoint(a)
+    elif a.workload == "series":
+        run_series(a)
     else:
         run_gpu(a)
 

@@ -16,7 +16,8 @@ NVCC = os.environ.get("NVCC", "nvcc")
 CU_SOURCES = ["lbm_api.cu", "kernels_f64.cu", "kernels_f32.cu",
               "kernels_f16dev.cu", "lbm_batch.cu"]
 CPP_SOURCES = ["geometry.cpp"]
-HEADERS = ["lbm_internal.h", "lbm_kernels.cuh", "lbm_launch_impl.cuh"]
+HEADERS = ["lbm_internal.h", "lbm_kernels.cuh", "lbm_launch_impl.cuh",
+           "lbm_tma.cuh", "lbm_f16.cuh"]
 
 
 def _cu_cmd(src, obj):

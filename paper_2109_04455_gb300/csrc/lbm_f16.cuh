@@ -1,0 +1,243 @@
+// FP16-deviation storage (populations stored as half of 2^14 (g - w_i R),
+// R the storing node's concentration, itself stored in half): the update of
+// an interior node, in a one-node form (used by the batch kernel) and a
+// two-node bulk kernel.  Included by lbm_kernels.cuh after AdrArgs and the
+// lattice helpers.
+#pragma once
+
+namespace lbm {
+
+// ---------------------------------------------------------------------------
+// Interior update of the FP16-deviation storage.  The arithmetic runs on the
+// populations scaled by 2^14, G = 2^14 g, the scale the deviations are
+// stored in, so a stored half converts straight into it; the concentration
+// is brought back to scale 1 once per species and node.  Scaling by a power
+// of two is exact, so every result equals the unscaled arithmetic's.  Each
+// operation is written with an explicit rounding (no contraction left to
+// the compiler), so the one-node form (batch kernel) and the two-node form
+// (bulk step) give the same bits for the same node.
+// ---------------------------------------------------------------------------
+namespace f16 {
+constexpr float kDown = 1.0f / 16384.0f, kUp = 16384.0f;
+__device__ __forceinline__ float w(int i) { return Lattice<float>::w(i); }
+// scaled population pulled from a source node: its stored deviation h plus
+// w_i times the source's scaled reference concentration rs = 2^14 R
+__device__ __forceinline__ float pull(int i, float h, float rs) {
+  return __fmaf_rn(w(i), rs, h);
+}
+__device__ __forceinline__ float scaled_ref(__half r) {
+  return __fmul_rn(__half2float(r), kUp);
+}
+// equilibrium factors E_i(u) = w_i (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
+__device__ __forceinline__ void eq(float ux, float uy, float (&E)[9]) {
+  const float base = __fmaf_rn(-1.5f, __fmaf_rn(ux, ux, __fmul_rn(uy, uy)), 1.0f);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float cu = __fadd_rn(float(cx(i)) * ux, float(cy(i)) * uy);
+    E[i] = __fmul_rn(w(i), __fmaf_rn(__fmul_rn(4.5f, cu), cu, __fmaf_rn(3.0f, cu, base)));
+  }
+}
+__device__ __forceinline__ float sum9(const float (&g)[9]) {
+  float c = g[0];
+#pragma unroll
+  for (int i = 1; i < 9; ++i) c = __fadd_rn(c, g[i]);
+  return c;
+}
+// value stored for population i: the BGK relaxation G + om (Cs E_i - G)
+// less w_i times the node's stored reference, all at scale 2^14 (cqs is
+// 2^14 times the half-rounded concentration)
+__device__ __forceinline__ float push(int i, float g, float cs, float e, float om,
+                                      float cqs) {
+  const float post = __fmaf_rn(om, __fmaf_rn(cs, e, -g), g);
+  return __fmaf_rn(-w(i), cqs, post);
+}
+}  // namespace f16
+
+template <int NS, int MODE>
+__device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long long n,
+                                                      float (&acc)[2 * NS]) {
+  const long long np = a.nx_pad, plane = a.plane;
+  const __half *__restrict__ src = static_cast<const __half *>(a.src);
+  __half *__restrict__ dst = static_cast<__half *>(a.dst);
+  const float *__restrict__ U = static_cast<const float *>(a.u);
+  float g[NS][9];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const long long m = n - (cy(i) * np + cx(i));
+      g[s][i] = f16::pull(i, __half2float(src[(long long)(s * 9 + i) * plane + m]),
+                          f16::scaled_ref(a.rsrc[s * plane + m]));
+    }
+  }
+  float *__restrict__ cp = static_cast<float *>(a.cprev);
+  float prev[NS];
+  if (MODE == kAdrCheck) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) prev[s] = cp[s * plane + n];
+  }
+  float E[9];
+  f16::eq(U[n], U[plane + n], E);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const float cs = f16::sum9(g[s]);
+    const float c = __fmul_rn(cs, f16::kDown);
+    const float cqs = __fmul_rn(ref_round(c), f16::kUp);
+    a.rdst[s * plane + n] = __float2half_rn(c);
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      dst[(long long)(s * 9 + i) * plane + n] =
+          __float2half_rn(f16::push(i, g[s][i], cs, E[i], a.fomega[s], cqs));
+    if (MODE == kAdrCheck) {
+      acc[2 * s] += fabsf(c - prev[s]);
+      acc[2 * s + 1] += fabsf(c);
+      cp[s * plane + n] = c;
+    }
+  }
+}
+
+// FP16 bulk step, two nodes per thread: nodes (x0, x0 + 1), x0 even, of row
+// y.  Every plane is read as aligned half2 pairs.  A pull with c_ix = +1
+// takes the sources (x0 - 1, x0): the high half of the pair to the left and
+// the low half of the node's own pair; c_ix = -1 takes (x0 + 1, x0 + 2)
+// from the own pair and the pair to the right.  The left pair is read only
+// when node x0 is interior (its neighbour x0 - 1 is a lattice node, so
+// x0 >= 2) and the right pair only when node x0 + 1 is interior (x0 + 2 <=
+// nx - 1, so x0 + 3 < nx_pad): every read stays inside its row, and rows
+// y +- 1 exist whenever either node is interior.  The reference
+// concentrations of the source nodes come the same way (three rows of three
+// pairs per species).  The arithmetic is that of adr_interior_node_f16.
+// Launched with kBlockX / 2 threads on the grid of adr_bulk_kernel, so a
+// block covers the same kBlockX nodes and writes the same partial-sum row.
+constexpr int kPairThreads = kBlockX / 2;
+template <int NS, int MODE>
+__global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
+    adr_bulk_pair_kernel(const AdrArgs a) {
+  const long long np = a.nx_pad, plane = a.plane;
+  const int y = blockIdx.y;
+  const int x0 = 2 * (blockIdx.x * kPairThreads + threadIdx.x);
+  const long long n0 = (long long)y * np + x0;
+  uint2 lw = make_uint2(kSolidNode, kSolidNode);
+  if (x0 < a.nx_pad) lw = *reinterpret_cast<const uint2 *>(a.links + n0);
+  const bool in0 = lw.x == 0u, in1 = lw.y == 0u;
+  float acc[2 * NS];
+#pragma unroll
+  for (int k = 0; k < 2 * NS; ++k) acc[k] = 0.0f;
+  if (in0 || in1) {
+    const __half *__restrict__ src = static_cast<const __half *>(a.src);
+    __half *__restrict__ dst = static_cast<__half *>(a.dst);
+    const __half2 z2 = __float2half2_rn(0.0f);
+    // all loads first: own pairs pc, side pairs pe (left for c_ix = +1,
+    // right for c_ix = -1), reference pairs of rows y - 1, y, y + 1
+    __half2 pc[NS][9], pe[NS][9], rc[NS][3], rl[NS][3], rr[NS][3];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const __half *row = src + (long long)(s * 9 + i) * plane +
+                            (long long)(y - cy(i)) * np + x0;
+        pc[s][i] = *reinterpret_cast<const __half2 *>(row);
+        if (cx(i) > 0) pe[s][i] = in0 ? *reinterpret_cast<const __half2 *>(row - 2) : z2;
+        if (cx(i) < 0) pe[s][i] = in1 ? *reinterpret_cast<const __half2 *>(row + 2) : z2;
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const __half *row = a.rsrc + (long long)s * plane + (long long)(y + r - 1) * np + x0;
+        rc[s][r] = *reinterpret_cast<const __half2 *>(row);
+        rl[s][r] = in0 ? *reinterpret_cast<const __half2 *>(row - 2) : z2;
+        rr[s][r] = in1 ? *reinterpret_cast<const __half2 *>(row + 2) : z2;
+      }
+    }
+    float *__restrict__ cp = static_cast<float *>(a.cprev);
+    float2 prev[NS];
+    if (MODE == kAdrCheck) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s)
+        prev[s] = *reinterpret_cast<const float2 *>(cp + s * plane + n0);
+    }
+    const float *__restrict__ U = static_cast<const float *>(a.u);
+    const float2 ux = *reinterpret_cast<const float2 *>(U + n0);
+    const float2 uy = *reinterpret_cast<const float2 *>(U + plane + n0);
+    float E0[9], E1[9];
+    f16::eq(ux.x, uy.x, E0);
+    f16::eq(ux.y, uy.y, E1);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      // scaled references of the source columns x0 - 1 .. x0 + 2, rows
+      // y - 1 .. y + 1 (the left / right column only where it is read)
+      float rs[3][4];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        rs[r][0] = f16::scaled_ref(__high2half(rl[s][r]));
+        rs[r][1] = f16::scaled_ref(__low2half(rc[s][r]));
+        rs[r][2] = f16::scaled_ref(__high2half(rc[s][r]));
+        rs[r][3] = f16::scaled_ref(__low2half(rr[s][r]));
+      }
+      float g0[9], g1[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const int r = 1 - cy(i);      // source row y - cy(i)
+        const int k = 1 - cx(i);      // column of node x0's source, x0 - 1 + k
+        __half h0, h1;
+        if (cx(i) == 0) {
+          h0 = __low2half(pc[s][i]);
+          h1 = __high2half(pc[s][i]);
+        } else if (cx(i) > 0) {
+          h0 = __high2half(pe[s][i]);
+          h1 = __low2half(pc[s][i]);
+        } else {
+          h0 = __high2half(pc[s][i]);
+          h1 = __low2half(pe[s][i]);
+        }
+        g0[i] = f16::pull(i, __half2float(h0), rs[r][k]);
+        g1[i] = f16::pull(i, __half2float(h1), rs[r][k + 1]);
+      }
+      const float cs0 = f16::sum9(g0), cs1 = f16::sum9(g1);
+      const float c0 = __fmul_rn(cs0, f16::kDown), c1 = __fmul_rn(cs1, f16::kDown);
+      const float cq0 = __fmul_rn(ref_round(c0), f16::kUp);
+      const float cq1 = __fmul_rn(ref_round(c1), f16::kUp);
+      const float om = a.fomega[s];
+      __half *o = dst + (long long)s * 9 * plane + n0;
+      __half *ro = a.rdst + (long long)s * plane + n0;
+      float *co = cp + s * plane + n0;
+      if (in0 && in1) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          *reinterpret_cast<__half2 *>(o + (long long)i * plane) =
+              __floats2half2_rn(f16::push(i, g0[i], cs0, E0[i], om, cq0),
+                                f16::push(i, g1[i], cs1, E1[i], om, cq1));
+        *reinterpret_cast<__half2 *>(ro) = __floats2half2_rn(c0, c1);
+        if (MODE == kAdrCheck) *reinterpret_cast<float2 *>(co) = make_float2(c0, c1);
+      } else {
+        // one interior node: the other belongs to the boundary kernel
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          if (in0) o[(long long)i * plane] = __float2half_rn(f16::push(i, g0[i], cs0, E0[i], om, cq0));
+          if (in1) o[(long long)i * plane + 1] = __float2half_rn(f16::push(i, g1[i], cs1, E1[i], om, cq1));
+        }
+        if (in0) ro[0] = __float2half_rn(c0);
+        if (in1) ro[1] = __float2half_rn(c1);
+        if (MODE == kAdrCheck) {
+          if (in0) co[0] = c0;
+          if (in1) co[1] = c1;
+        }
+      }
+      if (MODE == kAdrCheck) {
+        if (in0) {
+          acc[2 * s] += fabsf(c0 - prev[s].x);
+          acc[2 * s + 1] += fabsf(c0);
+        }
+        if (in1) {
+          acc[2 * s] += fabsf(c1 - prev[s].y);
+          acc[2 * s + 1] += fabsf(c1);
+        }
+      }
+    }
+  }
+  if (MODE == kAdrCheck) {
+    const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    block_sum_store<2 * NS, float>(acc, a.partials + b * (2 * NS));
+  }
+}
+
+}  // namespace lbm

@@ -176,6 +176,38 @@ def single_fiber(nx: int = 200, ny: int = 100, cx: float = 60.0,
                     r_ref=r, flow_steps=flow_steps, adr_steps=adr_steps)
 
 
+def isolated_fiber(pe: float, da: float, nx: int = 300, ny: int = 300,
+                   r: float = 5.0) -> Workload:
+    """Isolated A->B cylinder of Sec. II.B in the 2D channel: R = 5 in the
+    middle of a 300 x 300 box, species A and B."""
+    fib = fiber_table([[nx / 2.0, ny / 2.0, r, 1.0, 0.0, -1.0]])
+    return Workload(f"isolated_fiber_pe{pe:g}_da{da:g}", nx, ny, fib, 2,
+                    pe=pe, da1=da, da2=da, r_ref=r)
+
+
+def fiber_pair(xi: float, pe: float, da: float = 150.0, nx: int = 1000,
+               ny: int = 300, r: float = 5.0, x1: float = 300.0) -> Workload:
+    """Cascade on two single-catalyst cylinders of Sec. II.C: R = 5, an A->B
+    fiber at (x1, ny/2) and a B->C fiber downstream on the same streamline,
+    their surfaces xi apart (centres 2R + xi apart), 1000 x 300 box."""
+    x2 = x1 + 2.0 * r + xi
+    fib = fiber_table([[x1, ny / 2.0, r, 1.0, 0.0, -1.0],
+                       [x2, ny / 2.0, r, 2.0, 0.0, -1.0]])
+    return Workload(f"fiber_pair_xi{xi:g}_pe{pe:g}_da{da:g}", nx, ny, fib, 3,
+                    pe=pe, da1=da, da2=da, r_ref=r)
+
+
+def side_by_side_fiber(pe: float, da: float = 150.0, nx: int = 1000,
+                       ny: int = 300, r: float = 10.0,
+                       x1: float = 300.0) -> Workload:
+    """Side-by-side morphology of Sec. II.C: one R = 10 cylinder carrying
+    both catalysts, A->B on its upstream half and B->C on its downstream half
+    (interface across the flow), 1000 x 300 box."""
+    fib = fiber_table([[x1, ny / 2.0, r, 3.0, math.pi, -1.0]])
+    return Workload(f"side_by_side_pe{pe:g}_da{da:g}", nx, ny, fib, 3,
+                    pe=pe, da1=da, da2=da, r_ref=r)
+
+
 def two_membrane_cascade(seed: int = 0, pe: float = 10.0, nx: int = 2048,
                          ny: int = 512, bands=((400, 700), (1000, 1300)),
                          per_band: int = 40, r: int = 8,

@@ -1,0 +1,151 @@
+"""The paper's 2D experiment series, run on the batched lattice solver.
+
+* Isolated A->B fiber (Sec. II.B: R = 5 in the middle of a 300 x 300 box):
+  efficiency against Pe, next to the collision-zone model of Sec. IV.A.
+* A->B->C cascade (Sec. II.C, 1000 x 300 box, Da = 150) on two R = 5 fibers
+  whose surfaces are xi apart along the flow, and on one side-by-side R = 10
+  fiber; the model of Sec. IV.B for fibers far apart is the product of the
+  two single-fiber efficiencies.
+* Production rate of the final species (Appendix A).
+
+The inflow velocity u0 is fixed and Pe is set through D (so the flow depends
+only on the geometry): each geometry's flow is solved once, in FP64, and
+shared by all of its Pe values.  Every ADR lattice of one species count then
+advances in one lbm_batch.  Pe values whose rate k = Da D / R^2 reaches 1 per
+time step are left out (the explicit source empties a node in one step).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import inputs, lbm
+
+
+# ---------------------------------------------------------------------------
+# collision-zone model (Sec. IV.A)
+# ---------------------------------------------------------------------------
+def collision_zone(pe: float, r: float) -> float:
+    """Width d of the collision zone: positive root of Eq. (d),
+    d^2 / (2D) - (pi / u0) d - pi R / u0 = 0, written with Pe = u0 R / D:
+    d = R (pi/Pe + sqrt(pi^2/Pe^2 + 2 pi/Pe))."""
+    a = math.pi / pe
+    return r * (a + math.sqrt(a * a + 2.0 * math.pi / pe))
+
+
+def model_efficiency(pe: float, da: float, r: float, width: float,
+                     shell: float = 0.5) -> float:
+    """Eq. (eps): eps = eps_coll (1 - exp(-k alpha t_D)) with
+    eps_coll = d / (2 l) (half the molecules of the collision zone diffuse
+    towards the fiber, l the channel width; capped at 1), t_D = d^2 / (2D),
+    alpha = ((R + shell)^2 - R^2) / ((R + d)^2 - R^2) (the ratio of the
+    reaction shell's area to the collision zone's), k = Da D / R^2.  The
+    product k alpha t_D = Da alpha d^2 / (2 R^2) does not depend on u0."""
+    d = collision_zone(pe, r)
+    eps_coll = min(1.0, 0.5 * d / width)
+    alpha = ((r + shell) ** 2 - r * r) / ((r + d) ** 2 - r * r)
+    return eps_coll * (1.0 - math.exp(-da * alpha * d * d / (2.0 * r * r)))
+
+
+def production_rate(flux, ny: int, nspecies: int) -> float:
+    """Appendix A: final product leaving the reactor per time step (per unit
+    fiber length), N_final * ny with N_s the plane-averaged outflux."""
+    return float(flux[nspecies - 1]) * ny
+
+
+# ---------------------------------------------------------------------------
+# the series
+# ---------------------------------------------------------------------------
+DEFAULT_PE = (2.0, 3.0, 5.0, 7.0, 10.0, 20.0, 50.0, 100.0)
+
+
+def workloads(pes=DEFAULT_PE, xis=(2.0, 20.0, 100.0),
+              das_isolated=(150.0, 1.5)):
+    """(geometry key, workload) pairs of the series, k < 1 only."""
+    out = []
+    for da in das_isolated:
+        for pe in pes:
+            out.append(("isolated_fiber", inputs.isolated_fiber(pe, da)))
+    for xi in xis:
+        for pe in pes:
+            out.append((f"fiber_pair_xi{xi:g}", inputs.fiber_pair(xi, pe)))
+    for pe in pes:
+        out.append(("side_by_side", inputs.side_by_side_fiber(pe)))
+    return [(k, w) for k, w in out if max(w.k1, w.k2) < 1.0]
+
+
+def solve_flows(items, flow_tol: float = 1e-9, flow_max: int = 400000,
+                device="cuda"):
+    """FP64 flow of each distinct geometry key; returns {key: u}."""
+    flows = {}
+    for key, w in items:
+        if key in flows:
+            continue
+        g = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload(device)
+        u, info = lbm.lbm_flow_solve(g, w.tau_flow, w.u0, flow_max,
+                                     tol=flow_tol, check_every=1000,
+                                     precision=lbm.LBM_F64)
+        flows[key] = (u, info)
+    return flows
+
+
+def run(items=None, flows=None, precision: int = lbm.LBM_F32,
+        tol: float = 1e-6, max_steps: int = 200000, check_every: int = 1000,
+        device="cuda"):
+    """Steady efficiencies of the series.  Returns (rows, batches): one dict
+    per lattice (geometry key, Pe, Da, eps, model eps where the paper gives
+    one, production rate, steps, converged) and the Batch objects' launch
+    shapes."""
+    items = workloads() if items is None else items
+    flows = solve_flows(items, device=device) if flows is None else flows
+    rows = []
+    shapes = []
+    for ns in (2, 3):
+        sel = [(k, w) for k, w in items if w.nspecies == ns]
+        if not sel:
+            continue
+        geoms, params, us = [], [], []
+        for key, w in sel:
+            geoms.append(lbm.Geometry(w.nx, w.ny, w.fibers, w.k1,
+                                      w.k2).upload(device))
+            params.append(lbm.adr_params(ns, w.tau_c, w.c_in,
+                                         precision=precision,
+                                         max_steps=max_steps, tol=tol,
+                                         check_every=check_every))
+            u = flows[key][0]
+            us.append(u if precision == lbm.LBM_F64 else u.float())
+        b = lbm.Batch(geoms, params, us, device)
+        shapes.append(b.tune())
+        infos = b.solve()
+        b.close()
+        for (key, w), info in zip(sel, infos):
+            row = {"geometry": key, "pe": w.pe, "da": w.da1,
+                   "nx": w.nx, "ny": w.ny, "nspecies": ns,
+                   "eps": info["eps"], "flux": info["flux"][:ns],
+                   "production_rate": production_rate(info["flux"], w.ny, ns),
+                   "steps": info["steps"], "converged": info["converged"],
+                   "residual": info["residual"]}
+            if key == "isolated_fiber":
+                row["model_eps"] = model_efficiency(w.pe, w.da1, w.r_ref,
+                                                    float(w.ny))
+            rows.append(row)
+    # Eq. (eps_ABC) for the pairs: the square of one fiber's efficiency,
+    # stated for fibers whose collision zones do not overlap (xi > 2d)
+    for row, (key, w) in zip(rows, [it for ns in (2, 3) for it in items
+                                    if it[1].nspecies == ns]):
+        if key.startswith("fiber_pair"):
+            xi = w.fibers[1, 0] - w.fibers[0, 0] - 2.0 * w.r_ref
+            e1 = model_efficiency(w.pe, w.da1, w.r_ref, float(w.ny))
+            row["xi"] = float(xi)
+            row["model_eps"] = e1 * e1
+            row["model_applies"] = bool(xi > 2.0 * collision_zone(w.pe,
+                                                                  w.r_ref))
+    return rows, shapes
+
+
+def as_table(rows) -> np.ndarray:
+    """(geometry index, Pe, Da, eps) as an array, for plotting."""
+    keys = sorted({r["geometry"] for r in rows})
+    return np.array([[keys.index(r["geometry"]), r["pe"], r["da"], r["eps"]]
+                     for r in rows])

@@ -48,6 +48,9 @@ def test_exports_every_declared_symbol(lib):
     lambda: inputs.two_membrane_cascade(seed=1),
     lambda: inputs.sweep_instance(5),
     lambda: inputs.sweep_instance(42),
+    lambda: inputs.isolated_fiber(7.0, 150.0),
+    lambda: inputs.fiber_pair(2.0, 10.0),
+    lambda: inputs.side_by_side_fiber(10.0),
 ])
 def test_host_raster_matches_oracle(lib, make):
     w = make()
