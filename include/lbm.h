@@ -151,6 +151,12 @@ lbm_status lbm_flow_solve(const lbm_geometry *g, const lbm_flow_params *p,
 /* of the post-collision populations, accumulated in double.                  */
 /* ------------------------------------------------------------------------ */
 #define LBM_ADR_INLET_ABB_ALL 1 /* anti-bounce-back inlet for every species */
+/* Reaction variant the paper compares the link-wise source with (Fig.      */
+/* node_vs_pop): a fluid node with at least one link into a catalytic solid */
+/* node reacts on all nine populations, Q_i = w_i (-k_AB C_A, ...), with     */
+/* k_AB, k_BC the means of the rates over those links.  Not differentiable  */
+/* by lbm_adr_adjoint (LBM_EINVAL).                                          */
+#define LBM_ADR_NODEWISE 2
 
 typedef struct {
   int32_t nspecies;    /* 1 (A only), 2 (A->B) or 3 (A->B->C)               */

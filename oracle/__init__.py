@@ -54,6 +54,7 @@ PX = 1            # periodic in x
 PY = 2            # periodic in y
 ALLPOP = 4        # every population reacts with the node's own rates
 INLET_ABB_ALL = 8  # every species gets the inlet anti-bounce-back
+NODEWISE = 16     # a node with a catalytic link reacts on all populations
 
 Q = 9
 CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])

@@ -59,6 +59,10 @@ static const double CS2 = 1.0 / 3.0;
                                the node's own rates (homogeneous reaction)   */
 #define ORC_INLET_ABB_ALL 8 /* every species, not only A, gets the inlet
                                anti-bounce-back with its own c_in            */
+#define ORC_NODEWISE 16     /* a fluid node with a link into a catalytic
+                               solid node reacts on all its populations, with
+                               the mean rates of those links (the variant the
+                               paper compares against in Fig. node_vs_pop)   */
 
 /* Second-order equilibrium of Sec. III.A.2 for density/concentration c. */
 static double equilibrium(int i, double c, double ux, double uy) {
@@ -283,7 +287,10 @@ void orc_adr_conc(int nx, int ny, int ns, const uint8_t *solid,
  * into a solid lattice node (rates of that node):
  *   Q_A = -k_AB w C_A,  Q_B = +k_AB w C_A - k_BC w C_B,  Q_C = +k_BC w C_B,
  * all concentrations taken before collision at this node and time.  With
- * ORC_ALLPOP every population reacts with the node's own rates instead. */
+ * ORC_ALLPOP every population reacts with the node's own rates instead.
+ * With ORC_NODEWISE a node with at least one link into a catalytic solid
+ * node (non-zero k_AB or k_BC) reacts on every population i = 0..8, with
+ * k_AB, k_BC the means over those links. */
 static void adr_collide(int nx, int ny, int ns, const uint8_t *solid,
                         const double *kab, const double *kbc, double ux,
                         double uy, const double *tau, int flags, int x, int y,
@@ -298,6 +305,36 @@ static void adr_collide(int nx, int ny, int ns, const uint8_t *solid,
       double gi = g[(s * nn + n) * Q9 + i];
       gs[s][i] = gi - (gi - equilibrium(i, c[s], ux, uy)) / tau[s];
     }
+  if (flags & ORC_NODEWISE) {
+    double sa = 0.0, sb = 0.0;
+    int ncat = 0;
+    for (int i = 1; i < Q9; ++i) {
+      int tx = x + CX[i], ty = y + CY[i];
+      if (tx < 0 || tx >= nx) {
+        if (!(flags & ORC_PX)) continue;
+        tx = (tx + nx) % nx;
+      }
+      if (ty < 0 || ty >= ny) {
+        if (!(flags & ORC_PY)) continue;
+        ty = (ty + ny) % ny;
+      }
+      long t = (long)ty * nx + tx;
+      if (!solid[t] || (kab[t] == 0.0 && kbc[t] == 0.0)) continue;
+      sa += kab[t];
+      sb += kbc[t];
+      ++ncat;
+    }
+    if (ncat == 0) return;
+    double ka = sa / ncat, kb = sb / ncat;
+    for (int i = 0; i < Q9; ++i) {
+      double ra = ka * W[i] * c[0];
+      double rb = (ns >= 3) ? kb * W[i] * c[1] : 0.0;
+      gs[0][i] -= ra;
+      if (ns >= 2) gs[1][i] += ra - rb;
+      if (ns >= 3) gs[2][i] += rb;
+    }
+    return;
+  }
   for (int i = 0; i < Q9; ++i) {
     double ka = 0.0, kb = 0.0;
     if (flags & ORC_ALLPOP) {
@@ -523,7 +560,7 @@ int orc_adr_adjoint_steps(int nx, int ny, int ns, const uint8_t *solid,
                           const double *ux, const double *uy,
                           const double *tau, int flags, const double *dNds,
                           int xp, long nsteps, double *nu, double *tmp) {
-  if (ns < 1 || ns > 3 || (flags & ORC_ALLPOP)) return 1;
+  if (ns < 1 || ns > 3 || (flags & (ORC_ALLPOP | ORC_NODEWISE))) return 1;
   long nn = (long)nx * ny;
   long nt = (long)ns * nn * Q9;
   memset(tmp, 0, sizeof(double) * nt);

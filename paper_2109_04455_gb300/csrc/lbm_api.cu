@@ -340,6 +340,7 @@ static bool adr_params_ok(const lbm_adr_params *p) {
   if (p->precision < LBM_F64 || p->precision > LBM_F16DEV) return false;
   for (int s = 0; s < p->nspecies; ++s)
     if (!(p->tau[s] > 0.5) || !std::isfinite(p->c_in[s])) return false;
+  if (p->flags & ~(LBM_ADR_INLET_ABB_ALL | LBM_ADR_NODEWISE)) return false;
   return true;
 }
 
@@ -454,6 +455,7 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
   a.ny = g->ny;
   a.nx_pad = g->nx_pad;
   a.abb_all = (p->flags & LBM_ADR_INLET_ABB_ALL) ? 1 : 0;
+  a.nodewise = (p->flags & LBM_ADR_NODEWISE) ? 1 : 0;
   for (int k = 0; k < 3; ++k) {
     const bool on = k < p->nspecies;
     a.omega[k] = on ? 1.0 / p->tau[k] : 0.0;
@@ -516,6 +518,7 @@ static cudaError_t adr_step(lbm_adr_solver *s, int mode, cudaStream_t st) {
   a.dst = s->buf[s->cur ^ 1];
   a.rsrc = s->rbuf[s->cur];
   a.rdst = s->rbuf[s->cur ^ 1];
+  a.step = static_cast<unsigned>(s->steps);
   s->cur ^= 1;
   ++s->steps;
   return adr_launch(s->p.precision, s->p.nspecies, mode, a, st, &s->ov);
@@ -701,6 +704,10 @@ extern "C" lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps,
   const int prec = s->p.precision;
   if (ns < 2 || prec == LBM_F16DEV) {
     set_error("lbm_adr_adjoint: needs 2 or 3 species and LBM_F64 / LBM_F32");
+    return LBM_EINVAL;
+  }
+  if (s->p.flags & LBM_ADR_NODEWISE) {
+    set_error("lbm_adr_adjoint: the node-wise reaction variant has no adjoint");
     return LBM_EINVAL;
   }
   if (!s->has_check) {

@@ -502,6 +502,7 @@ extern "C" lbm_status lbm_batch_create(int32_t count,
     a.ny = g->ny;
     a.nx_pad = g->nx_pad;
     a.abb_all = (p.flags & LBM_ADR_INLET_ABB_ALL) ? 1 : 0;
+    a.nodewise = (p.flags & LBM_ADR_NODEWISE) ? 1 : 0;
     a.xp = p.x_plane < 0 ? g->nx - 3 : p.x_plane;
     for (int k = 0; k < 3; ++k) {
       const bool on = k < p.nspecies;

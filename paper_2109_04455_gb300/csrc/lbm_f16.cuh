@@ -51,6 +51,37 @@ __device__ __forceinline__ float push(int i, float g, float cs, float e, float o
   const float post = __fmaf_rn(om, __fmaf_rn(cs, e, -g), g);
   return __fmaf_rn(-w(i), cqs, post);
 }
+
+// Rounding of a scaled population to half.  LBM_F16_SR = 1: stochastic
+// rounding, the float's 13 mantissa bits below half precision get a random
+// 13-bit number added before truncation, so a value rounds up with
+// probability equal to its distance from the lower neighbour; the random
+// bits come from a hash of (node pair, step) times a per-store odd constant.
+#ifndef LBM_F16_SR
+#define LBM_F16_SR 0
+#endif
+__device__ __forceinline__ uint32_t pair_hash(long long pair, unsigned step) {
+  uint32_t h = static_cast<uint32_t>(pair) * 0x9E3779B1u ^
+               static_cast<uint32_t>(pair >> 32) * 0x7FEB352Du ^
+               (step + 0x632BE5ABu) * 0x85EBCA77u;
+  h ^= h >> 16;
+  h *= 0x7FEB352Du;
+  h ^= h >> 15;
+  h *= 0x846CA68Bu;
+  h ^= h >> 16;
+  return h;
+}
+// k: store index of the node pair (0 .. 2 * 27 - 1)
+__device__ __forceinline__ __half round_half(float v, uint32_t h, int k) {
+#if LBM_F16_SR
+  const uint32_t r = (h * (0x9E3779B1u + 2u * static_cast<uint32_t>(k))) >> 19;
+  return __float2half_rz(__uint_as_float(__float_as_uint(v) + r));
+#else
+  (void)h;
+  (void)k;
+  return __float2half_rn(v);
+#endif
+}
 }  // namespace f16
 
 template <int NS, int MODE>
@@ -78,6 +109,8 @@ __device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long lon
   }
   float E[9];
   f16::eq(U[n], U[plane + n], E);
+  const uint32_t h = f16::pair_hash(n >> 1, a.step);
+  const int kn = static_cast<int>(n & 1) * 27;   // second node of its pair
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     const float cs = f16::sum9(g[s]);
@@ -86,8 +119,8 @@ __device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long lon
     a.rdst[s * plane + n] = __float2half_rn(c);
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-      dst[(long long)(s * 9 + i) * plane + n] =
-          __float2half_rn(f16::push(i, g[s][i], cs, E[i], a.fomega[s], cqs));
+      dst[(long long)(s * 9 + i) * plane + n] = f16::round_half(
+          f16::push(i, g[s][i], cs, E[i], a.fomega[s], cqs), h, kn + s * 9 + i);
     if (MODE == kAdrCheck) {
       acc[2 * s] += fabsf(c - prev[s]);
       acc[2 * s + 1] += fabsf(c);
@@ -161,6 +194,7 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
     float E0[9], E1[9];
     f16::eq(ux.x, uy.x, E0);
     f16::eq(ux.y, uy.y, E1);
+    const uint32_t hp = f16::pair_hash(n0 >> 1, a.step);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
       // scaled references of the source columns x0 - 1 .. x0 + 2, rows
@@ -203,17 +237,17 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
       if (in0 && in1) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-          *reinterpret_cast<__half2 *>(o + (long long)i * plane) =
-              __floats2half2_rn(f16::push(i, g0[i], cs0, E0[i], om, cq0),
-                                f16::push(i, g1[i], cs1, E1[i], om, cq1));
+          *reinterpret_cast<__half2 *>(o + (long long)i * plane) = __halves2half2(
+              f16::round_half(f16::push(i, g0[i], cs0, E0[i], om, cq0), hp, s * 9 + i),
+              f16::round_half(f16::push(i, g1[i], cs1, E1[i], om, cq1), hp, 27 + s * 9 + i));
         *reinterpret_cast<__half2 *>(ro) = __floats2half2_rn(c0, c1);
         if (MODE == kAdrCheck) *reinterpret_cast<float2 *>(co) = make_float2(c0, c1);
       } else {
         // one interior node: the other belongs to the boundary kernel
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-          if (in0) o[(long long)i * plane] = __float2half_rn(f16::push(i, g0[i], cs0, E0[i], om, cq0));
-          if (in1) o[(long long)i * plane + 1] = __float2half_rn(f16::push(i, g1[i], cs1, E1[i], om, cq1));
+          if (in0) o[(long long)i * plane] = f16::round_half(f16::push(i, g0[i], cs0, E0[i], om, cq0), hp, s * 9 + i);
+          if (in1) o[(long long)i * plane + 1] = f16::round_half(f16::push(i, g1[i], cs1, E1[i], om, cq1), hp, 27 + s * 9 + i);
         }
         if (in0) ro[0] = __float2half_rn(c0);
         if (in1) ro[1] = __float2half_rn(c1);

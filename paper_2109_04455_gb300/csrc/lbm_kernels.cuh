@@ -193,6 +193,8 @@ struct AdrArgs {
   int nx, ny, nx_pad;
   int *status;              // device word: non-zero after a failed wait
   int abb_all;              // anti-bounce-back inlet for every species
+  int nodewise;             // every population of a reactive node reacts
+  unsigned step;            // steps done before this one (rounding seed)
   int xp;                   // flux plane
   double omega[3];          // 1/tau per species
   double cin[3];            // inlet concentration per species
@@ -283,6 +285,8 @@ __device__ __forceinline__ void adr_boundary(const AdrArgs &a, int s,
 // BGK collision of species s towards C E_i, then its Dawson source on links
 // into catalytic fiber nodes (Eq. source_lbm):
 //   Q_A = -k_AB w C_A,  Q_B = +k_AB w C_A - k_BC w C_B,  Q_C = +k_BC w C_B.
+// With a.nodewise, a node with catalytic links reacts on all nine
+// populations instead, with the mean rates of those links.
 // C[] holds the pre-collision concentrations of species 0..s; returns C_s.
 template <class P, int NS>
 __device__ __forceinline__ typename P::T adr_collide(const AdrArgs &a, int s,
@@ -298,7 +302,35 @@ __device__ __forceinline__ typename P::T adr_collide(const AdrArgs &a, int s,
   const T om = pick<T>(a.omega[s], a.fomega[s]);
 #pragma unroll
   for (int i = 0; i < 9; ++i) g[i] = g[i] + om * (c * E[i] - g[i]);
-  if (lw != 0u) {
+  if (lw != 0u && a.nodewise) {
+    const long long np = a.nx_pad;
+    T sa = T(0), sb = T(0);
+    int ncat = 0;
+#pragma unroll
+    for (int j = 1; j < 9; ++j) {
+      if (nib(lw, j) != kCat) continue;
+      const long long m = n + cy(j) * np + cx(j);
+      sa += T(a.kab[m]);
+      sb += T(a.kbc[m]);
+      ++ncat;
+    }
+    if (ncat > 0) {
+      const T ka = sa / T(ncat), kb = sb / T(ncat);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const T wi = Lattice<T>::w(i);
+        if (s == 0) {
+          g[i] -= ka * wi * C[0];
+        } else if (s == 1) {
+          const T ra = ka * wi * C[0];
+          const T rb = (NS >= 3) ? kb * wi * C[NS >= 2 ? 1 : 0] : T(0);
+          g[i] += ra - rb;
+        } else {
+          g[i] += kb * wi * C[NS >= 2 ? 1 : 0];
+        }
+      }
+    }
+  } else if (lw != 0u) {
     const long long np = a.nx_pad;
 #pragma unroll
     for (int j = 1; j < 9; ++j) {

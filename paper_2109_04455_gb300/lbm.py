@@ -24,6 +24,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTCONVERGED, \
     LBM_EUNSTABLE = range(6)
 LBM_F64, LBM_F32, LBM_F16DEV = range(3)
 LBM_ADR_INLET_ABB_ALL = 1
+LBM_ADR_NODEWISE = 2
 PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16dev": LBM_F16DEV}
 
 _STATUS = {LBM_EINVAL: "EINVAL", LBM_ENOMEM: "ENOMEM", LBM_ECUDA: "ECUDA",

@@ -159,3 +159,20 @@ def test_autograd_function_matches_finite_differences():
             vals.append(float(prob.efficiency(w2)))
         fd = (vals[0] - vals[1]) / (2 * h)
         assert g[f] == pytest.approx(fd, rel=1e-3, abs=1e-3 * np.abs(g).max())
+
+
+def test_adjoint_refuses_nodewise_variant():
+    """The node-wise reaction variant has no adjoint: LBM_EINVAL, and the
+    solver stays usable."""
+    nx, ny, fib, k1, k2 = _geometry()
+    geom = lbm.Geometry(nx, ny, fib, k1, k2).upload()
+    u = torch.zeros((2, ny, geom.nx_pad), dtype=torch.float64, device="cuda")
+    u[0, :, :nx] = 0.02
+    prm = lbm.adr_params(3, [0.62] * 3, precision=lbm.LBM_F64,
+                         flags=lbm.LBM_ADR_NODEWISE)
+    sv = lbm.ADRSolver(geom, prm, u).init()
+    sv.run(10)
+    with pytest.raises(lbm.LBMError) as e:
+        sv.adjoint(10)
+    assert e.value.status == lbm.LBM_EINVAL
+    assert sv.run(10)["steps"] == 20

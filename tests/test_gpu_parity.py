@@ -140,9 +140,15 @@ def _oracle_case(name, flow_steps=300):
     return nx, ny, fib, k1, k2, solid, kab, kbc, ux, uy
 
 
+_ORACLE_FLAGS = {0: 0, lbm.LBM_ADR_INLET_ABB_ALL: oracle.INLET_ABB_ALL,
+                 lbm.LBM_ADR_NODEWISE: oracle.NODEWISE}
+
+
 @pytest.mark.parametrize("name,ns,flags", [
     ("small", 3, 0), ("small", 2, 0), ("small", 1, 0),
     ("ragged", 3, 0), ("ragged", 3, lbm.LBM_ADR_INLET_ABB_ALL),
+    ("small", 3, lbm.LBM_ADR_NODEWISE), ("ragged", 2, lbm.LBM_ADR_NODEWISE),
+    ("ragged", 3, lbm.LBM_ADR_NODEWISE | lbm.LBM_ADR_INLET_ABB_ALL),
     ("empty", 2, 0)])
 def test_adr_f64_matches_oracle(name, ns, flags):
     nx, ny, fib, k1, k2, solid, kab, kbc, ux, uy = _oracle_case(name)
@@ -153,8 +159,12 @@ def test_adr_f64_matches_oracle(name, ns, flags):
     u = _dev_u(ux, uy, geom.nx_pad, torch.float64)
     conc, info = _run_gpu_adr(geom, u, ns, taus, cin, lbm.LBM_F64, steps,
                               flags)
+    oflags = 0
+    for bit, obit in _ORACLE_FLAGS.items():
+        if flags & bit:
+            oflags |= obit
     prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, taus, cin,
-                             flags=oracle.INLET_ABB_ALL if flags else 0)
+                             flags=oflags)
     ref = prob.run(steps)
     rel = np.linalg.norm(conc - ref["conc"]) / np.linalg.norm(ref["conc"])
     assert rel < 1e-10

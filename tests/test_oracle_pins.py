@@ -80,8 +80,8 @@ def test_raster_janus_and_relaxed_weight():
 def test_homogeneous_cascade_closed_form(k1, k2):
     """Periodic, u = 0, every population reacts: the discrete law is
     C_A(t) = (1-k1)^t, C_B(t) = k1/(k2-k1) [(1-k1)^t - (1-k2)^t],
-    C_C = 1 - C_A - C_B; with k1 = 1 A vanishes after one step
-    (Appendix C: 'decays to zero instantaneously')."""
+    C_C = 1 - C_A - C_B; with k1 = 1 A vanishes after one step, as the
+    homogeneous-reaction check of Appendix C states for k = 1."""
     nx, ny = 6, 5
     solid = np.zeros((ny, nx), np.uint8)
     z = np.zeros((ny, nx))
@@ -103,6 +103,40 @@ def test_homogeneous_cascade_closed_form(k1, k2):
         prob.steps(g, 1)
         # zero up to the rounding of sum_i w_i = 1
         assert np.abs(prob.conc(g)[0]).max() < 1e-15
+
+
+@pytest.mark.parametrize("k1,k2", [(0.05, 0.02), (0.3, 0.6)])
+def test_nodewise_reactive_lattice_closed_form(k1, k2):
+    """Node-wise variant (every population of a node with catalytic links
+    reacts, with the mean rates of those links): periodic lattice with an
+    isolated catalytic solid node at every (odd x, odd y), so every fluid
+    node has catalytic links, all with the same rates.  With u = 0 the fluid
+    state stays uniform (bounce-back returns w_i C like a uniform neighbour)
+    and follows the homogeneous law C_A = (1-k1)^t,
+    C_B = k1/(k2-k1) [(1-k1)^t - (1-k2)^t].  The link-wise source on the
+    same lattice reacts less per step (fewer than nine links react)."""
+    nx, ny = 8, 6
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[1::2, 1::2] = 1
+    kab = np.where(solid == 1, k1, 0.0)
+    kbc = np.where(solid == 1, k2, 0.0)
+    z = np.zeros((ny, nx))
+    fluid = solid == 0
+    prob = oracle.ADRProblem(solid, kab, kbc, z, z, [0.9] * 3, [0, 0, 0],
+                             flags=oracle.PX | oracle.PY | oracle.NODEWISE)
+    link = oracle.ADRProblem(solid, kab, kbc, z, z, [0.9] * 3, [0, 0, 0],
+                             flags=oracle.PX | oracle.PY)
+    g, gl = prob.init(), link.init()
+    for t in range(1, 31):
+        prob.steps(g, 1)
+        link.steps(gl, 1)
+        c = prob.conc(g)
+        a = (1 - k1) ** t
+        b = k1 / (k2 - k1) * ((1 - k1) ** t - (1 - k2) ** t)
+        assert np.allclose(c[0][fluid], a, rtol=1e-12, atol=1e-15)
+        assert np.allclose(c[1][fluid], b, rtol=1e-12, atol=1e-16)
+        assert np.allclose(c[2][fluid], 1 - a - b, rtol=1e-12, atol=1e-15)
+    assert link.conc(gl)[0][fluid].mean() > a * 1.01
 
 
 def test_homogeneous_decay_vs_exponential_small_k():
@@ -296,15 +330,17 @@ def _small_channel(nx=64, ny=24, steps=300):
     return solid, kab, kbc, ux, uy
 
 
-def test_species_sum_invariant_cascade():
+@pytest.mark.parametrize("variant", [0, oracle.NODEWISE])
+def test_species_sum_invariant_cascade(variant):
     """Eq. (source_lbm): the sources of A, B and C on each link add to zero,
     so with equal tau and the same anti-bounce-back inlet for every species
     (test mode, C_w = 1, 0, 0) the field C_A+C_B+C_C equals, at every node
-    and step, that of one non-reacting species."""
+    and step, that of one non-reacting species.  The same holds for the
+    node-wise variant (its sources add to zero on every population)."""
     solid, kab, kbc, ux, uy = _small_channel()
     tau = 0.62
     p3 = oracle.ADRProblem(solid, kab, kbc, ux, uy, [tau] * 3, [1, 0, 0],
-                           flags=oracle.INLET_ABB_ALL)
+                           flags=oracle.INLET_ABB_ALL | variant)
     p1 = oracle.ADRProblem(solid, kab * 0, kbc * 0, ux, uy, [tau], [1.0],
                            flags=oracle.INLET_ABB_ALL)
     g3, g1 = p3.init(), p1.init()
