@@ -620,8 +620,8 @@ def run_adjoint(a):
 # ---------------------------------------------------------------------------
 def run_series(a):
     """Isolated A->B fiber (Da = 150, 1.5), A->B->C fiber pairs at xi = 2,
-    20, 100 and the side-by-side fiber (Da = 150), Pe = 2..100: 48 lattices
-    of 300x300 and 1000x300.  Untimed: one FP64 flow per geometry.  Timed
+    20, 100 and the side-by-side fiber (Da = 150), Pe = 1..30 where k < 1
+    and tau_c >= 0.52: 44 lattices of 300x300 and 1000x300.  Untimed: one FP64 flow per geometry.  Timed
     on the host clock (the solves end synchronised): the launch-shape tuning
     and the batched ADR solves (two batches, 2 and 3 species) to a per-step
     residual of 1e-7 or the 300000-step cap.  Reports solves/s, and per lattice the efficiency, the

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -39,16 +40,24 @@ __host__ __device__ inline unsigned long long chunk_item(int inst,
          static_cast<unsigned long long>(start);
 }
 
+// stepc[parity]: steps every active instance has done before this one (all
+// start together); the launch passes it to the per-node updates as
+// AdrArgs::step (the rounding seed of half storage) and leaves the next
+// count in stepc[parity ^ 1] for the next launch.
 template <class P, int NS, int MODE, int BX>
 __global__ void __launch_bounds__(BX)
     batch_step_kernel(const AdrArgs *__restrict__ table, int parity,
                       const unsigned long long *__restrict__ work,
-                      long long nwork, double *partials) {
+                      long long nwork, double *partials, unsigned *stepc) {
   using T = typename P::T;
   __shared__ AdrArgs sa;
   constexpr int kWords = sizeof(AdrArgs) / sizeof(unsigned long long);
   static_assert(sizeof(AdrArgs) % sizeof(unsigned long long) == 0,
                 "AdrArgs is copied as 8-byte words");
+  constexpr int kStepWord = static_cast<int>(offsetof(AdrArgs, step) / 8);
+  constexpr int kStepShift = static_cast<int>(offsetof(AdrArgs, step) % 8) * 8;
+  const unsigned step = stepc[parity];
+  if (blockIdx.x == 0 && threadIdx.x == 0) stepc[parity ^ 1] = step + 1u;
   for (long long w = blockIdx.x; w < nwork; w += gridDim.x) {
     const unsigned long long item = work[w];
     const int inst = static_cast<int>((item >> 48) & 0x7fff);
@@ -57,7 +66,13 @@ __global__ void __launch_bounds__(BX)
       const unsigned long long *srcw =
           reinterpret_cast<const unsigned long long *>(table + 2 * inst + parity);
       unsigned long long *dstw = reinterpret_cast<unsigned long long *>(&sa);
-      for (int k = threadIdx.x; k < kWords; k += BX) dstw[k] = srcw[k];
+      for (int k = threadIdx.x; k < kWords; k += BX) {
+        unsigned long long v = srcw[k];
+        if (k == kStepWord)
+          v = (v & ~(0xFFFFFFFFull << kStepShift)) |
+              (static_cast<unsigned long long>(step) << kStepShift);
+        dstw[k] = v;
+      }
     }
     __syncthreads();
     T acc[2 * NS];
@@ -135,17 +150,18 @@ __global__ void __launch_bounds__(kReduceThreads)
 template <class P, int NS>
 cudaError_t launch_step(int mode, int bx, const AdrArgs *table, int parity,
                         const unsigned long long *work, long long nwork,
-                        double *partials, unsigned grid, cudaStream_t st) {
+                        double *partials, unsigned *stepc, unsigned grid,
+                        cudaStream_t st) {
   if (bx == 128) {
     if (mode == kAdrCheck)
-      batch_step_kernel<P, NS, kAdrCheck, 128><<<grid, 128, 0, st>>>(table, parity, work, nwork, partials);
+      batch_step_kernel<P, NS, kAdrCheck, 128><<<grid, 128, 0, st>>>(table, parity, work, nwork, partials, stepc);
     else
-      batch_step_kernel<P, NS, kAdrStep, 128><<<grid, 128, 0, st>>>(table, parity, work, nwork, partials);
+      batch_step_kernel<P, NS, kAdrStep, 128><<<grid, 128, 0, st>>>(table, parity, work, nwork, partials, stepc);
   } else {
     if (mode == kAdrCheck)
-      batch_step_kernel<P, NS, kAdrCheck, 256><<<grid, 256, 0, st>>>(table, parity, work, nwork, partials);
+      batch_step_kernel<P, NS, kAdrCheck, 256><<<grid, 256, 0, st>>>(table, parity, work, nwork, partials, stepc);
     else
-      batch_step_kernel<P, NS, kAdrStep, 256><<<grid, 256, 0, st>>>(table, parity, work, nwork, partials);
+      batch_step_kernel<P, NS, kAdrStep, 256><<<grid, 256, 0, st>>>(table, parity, work, nwork, partials, stepc);
   }
   return cudaGetLastError();
 }
@@ -153,12 +169,12 @@ cudaError_t launch_step(int mode, int bx, const AdrArgs *table, int parity,
 template <class P>
 cudaError_t launch_step_p(int ns, int mode, int bx, const AdrArgs *table,
                           int parity, const unsigned long long *work,
-                          long long nwork, double *partials, unsigned grid,
-                          cudaStream_t st) {
+                          long long nwork, double *partials, unsigned *stepc,
+                          unsigned grid, cudaStream_t st) {
   return ns == 2 ? launch_step<P, 2>(mode, bx, table, parity, work, nwork,
-                                     partials, grid, st)
+                                     partials, stepc, grid, st)
                  : launch_step<P, 3>(mode, bx, table, parity, work, nwork,
-                                     partials, grid, st);
+                                     partials, stepc, grid, st);
 }
 
 template <class P>
@@ -206,6 +222,7 @@ struct lbm_batch {
   long long *d_rows = nullptr;
   double *d_sums = nullptr;             // [count][2*ns]
   double *d_flux = nullptr;             // [count][3]
+  unsigned *d_step = nullptr;           // [2] step count, ping-pong
   long long max_items = 0;
   // state
   int parity = 0;
@@ -243,7 +260,7 @@ size_t store_b(int prec) { return prec == LBM_F64 ? 8 : (prec == LBM_F32 ? 4 : 2
 size_t comp_b(int prec) { return prec == LBM_F64 ? 8 : 4; }
 
 struct BatchLayout {
-  size_t table, work, partials, rows, sums, flux, head, total;
+  size_t table, work, partials, rows, sums, flux, step, head, total;
   std::vector<size_t> inst_off;  // start of each instance's buffers
   std::vector<size_t> buf;       // bytes of one population buffer
   std::vector<size_t> cprev;
@@ -262,7 +279,8 @@ BatchLayout batch_layout(int count, const lbm_geometry *const *geoms,
   l.rows = a256(8 * 2 * count);
   l.sums = a256(8 * 2 * ns * count);
   l.flux = a256(8 * 3 * count);
-  l.head = l.table + l.work + l.partials + l.rows + l.sums + l.flux;
+  l.step = a256(2 * sizeof(unsigned));
+  l.head = l.table + l.work + l.partials + l.rows + l.sums + l.flux + l.step;
   size_t off = l.head;
   for (int i = 0; i < count; ++i) {
     const size_t pl = static_cast<size_t>(geoms[i]->nx_pad) * geoms[i]->ny;
@@ -300,13 +318,13 @@ cudaError_t step_launch(lbm_batch *b, int mode, int parity, cudaStream_t st) {
   switch (b->prec) {
     case LBM_F64:
       return launch_step_p<PrecF64>(b->ns, mode, b->bx, b->d_table, parity,
-                                    b->d_work, b->nwork, b->d_partials, b->grid, st);
+                                    b->d_work, b->nwork, b->d_partials, b->d_step, b->grid, st);
     case LBM_F32:
       return launch_step_p<PrecF32>(b->ns, mode, b->bx, b->d_table, parity,
-                                    b->d_work, b->nwork, b->d_partials, b->grid, st);
+                                    b->d_work, b->nwork, b->d_partials, b->d_step, b->grid, st);
     default:
       return launch_step_p<PrecF16Dev>(b->ns, mode, b->bx, b->d_table, parity,
-                                       b->d_work, b->nwork, b->d_partials, b->grid, st);
+                                       b->d_work, b->nwork, b->d_partials, b->d_step, b->grid, st);
   }
 }
 
@@ -414,6 +432,8 @@ lbm_status init_states(lbm_batch *b, cudaStream_t st) {
     if (e != cudaSuccess) return bfail("lbm_batch(init)", e);
     b->steps[i] = 0;
   }
+  cudaError_t e = cudaMemsetAsync(b->d_step, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return bfail("lbm_batch(init)", e);
   b->parity = 0;
   return LBM_OK;
 }
@@ -477,6 +497,8 @@ extern "C" lbm_status lbm_batch_create(int32_t count,
   b->d_sums = reinterpret_cast<double *>(base + l.table + l.work + l.partials + l.rows);
   b->d_flux = reinterpret_cast<double *>(base + l.table + l.work + l.partials +
                                          l.rows + l.sums);
+  b->d_step = reinterpret_cast<unsigned *>(base + l.table + l.work + l.partials +
+                                           l.rows + l.sums + l.flux);
   b->active.assign(count, 1);
   b->steps.assign(count, 0);
   int ce = params[0].check_every < 2 ? 100 : params[0].check_every;

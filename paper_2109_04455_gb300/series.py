@@ -12,7 +12,10 @@ The inflow velocity u0 is fixed and Pe is set through D (so the flow depends
 only on the geometry): each geometry's flow is solved once, in FP64, and
 shared by all of its Pe values.  Every ADR lattice of one species count then
 advances in one lbm_batch.  Pe values whose rate k = Da D / R^2 reaches 1 per
-time step are left out (the explicit source empties a node in one step).
+time step are left out (the explicit source empties a node in one step), and
+so are those whose tau_c = 3 D + 1/2 falls below 0.52 (with u0 = 0.05 the BGK
+advection-diffusion lattice goes unstable there: Pe = 100 at R = 5 gives
+tau_c = 0.5075 and a non-finite state).
 """
 from __future__ import annotations
 
@@ -57,12 +60,14 @@ def production_rate(flux, ny: int, nspecies: int) -> float:
 # ---------------------------------------------------------------------------
 # the series
 # ---------------------------------------------------------------------------
-DEFAULT_PE = (2.0, 3.0, 5.0, 7.0, 10.0, 20.0, 50.0, 100.0)
+DEFAULT_PE = (1.0, 2.0, 3.0, 5.0, 7.0, 10.0, 20.0, 30.0)
+TAU_MIN = 0.52
 
 
 def workloads(pes=DEFAULT_PE, xis=(2.0, 20.0, 100.0),
               das_isolated=(150.0, 1.5)):
-    """(geometry key, workload) pairs of the series, k < 1 only."""
+    """(geometry key, workload) pairs of the series with k < 1 and
+    tau_c >= TAU_MIN."""
     out = []
     for da in das_isolated:
         for pe in pes:
@@ -72,7 +77,8 @@ def workloads(pes=DEFAULT_PE, xis=(2.0, 20.0, 100.0),
             out.append((f"fiber_pair_xi{xi:g}", inputs.fiber_pair(xi, pe)))
     for pe in pes:
         out.append(("side_by_side", inputs.side_by_side_fiber(pe)))
-    return [(k, w) for k, w in out if max(w.k1, w.k2) < 1.0]
+    return [(k, w) for k, w in out
+            if max(w.k1, w.k2) < 1.0 and w.tau_c >= TAU_MIN]
 
 
 def solve_flows(items, flow_tol: float = 1e-9, flow_max: int = 400000,
