@@ -389,7 +389,13 @@ def run_gpu(a):
         dist.barrier()
     elapsed = t0.elapsed_time(t1) * 1e-3
     plain_s = sum(e0.elapsed_time(e1) for e0, e1 in ev_plain) * 1e-3
-    launches_per_step = CHUNK + 2   # steps + partial-sum reduce + flux
+    # per ADR step the bulk kernel and (when the lattice has boundary nodes)
+    # the boundary-node kernel; per bench step the two-level partial-sum
+    # reduce (2 launches) and the outflux kernel
+    import numpy as np
+    lw = geom.ws[:4 * geom.nx_pad * geom.ny].view(torch.int32).cpu().numpy()
+    has_bnd = bool(((lw != 0) & (lw != -1)).any())
+    launches_per_step = CHUNK * (2 if has_bnd else 1) + 3
     elapsed = max_over_ranks(elapsed, dev)
     updates = SPECIES * w.nx * w.ny * CHUNK * a.steps
     value = job_throughput(updates, world, elapsed)

@@ -94,6 +94,21 @@ lbm_status lbm_geometry_info(const lbm_geometry *g, int32_t *nx_pad,
 lbm_status lbm_geometry_fields(const lbm_geometry *g, uint8_t *solid,
                                double *kab, double *kbc);
 
+/* Replace the per-node rates by host fields kab, kbc (ny*nx doubles each,
+ * row-major, unpadded; either may be NULL to keep that rate): any catalyst
+ * distribution over the solid nodes, e.g. one that follows the per-node
+ * gradients of lbm_adr_adjoint.  Rates must be finite, >= 0 and zero on
+ * fluid nodes (LBM_EINVAL otherwise, nothing changed).  The link words are
+ * rebuilt (a solid node is catalytic when either rate is non-zero).  The
+ * device copy is stale afterwards: call lbm_geometry_upload again (same
+ * workspace size) before creating solvers; solvers created earlier keep
+ * reading the device copy until that upload overwrites it.  The per-fiber
+ * weight gradient of lbm_adr_adjoint assumes the relaxed assignment
+ * k_AB = w k1, k_BC = (1 - w) k2; its per-node gradients hold for any
+ * rates. */
+lbm_status lbm_geometry_set_rates(lbm_geometry *g, const double *kab,
+                                  const double *kbc);
+
 /* Device bytes lbm_geometry_upload needs. */
 size_t lbm_geometry_ws_bytes(const lbm_geometry *g);
 

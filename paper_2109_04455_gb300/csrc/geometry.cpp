@@ -13,6 +13,49 @@
 
 using namespace lbm;
 
+namespace {
+
+// Link words of the fluid nodes (nibble j-1: type of the neighbour x + c_j,
+// a solid neighbour being catalytic when either of its rates is non-zero),
+// the boundary-node list and the solid count.
+void build_links(lbm_geometry *g) {
+  const int64_t nx = g->nx, ny = g->ny;
+  g->links.assign(static_cast<size_t>(g->nx_pad) * ny, kSolidNode);
+  g->bnodes.clear();
+  int64_t nsol = 0;
+  for (int64_t y = 0; y < ny; ++y) {
+    for (int64_t x = 0; x < nx; ++x) {
+      const int64_t n = y * g->nx_pad + x;
+      if (g->solid[y * nx + x]) {
+        ++nsol;
+        continue;  // stays kSolidNode
+      }
+      uint32_t word = 0;
+      for (int j = 1; j < 9; ++j) {
+        const int64_t tx = x + kCx[j], ty = y + kCy[j];
+        uint32_t t;
+        if (tx < 0)
+          t = kInlet;  // the x-boundary rule wins on corner links
+        else if (tx >= nx)
+          t = kOutlet;
+        else if (ty < 0 || ty >= ny)
+          t = kWall;
+        else if (g->solid[ty * nx + tx]) {
+          const int64_t m = ty * g->nx_pad + tx;
+          t = (g->kab[m] != 0.0 || g->kbc[m] != 0.0) ? kCat : kInert;
+        } else
+          t = kFluid;
+        word |= t << (4 * (j - 1));
+      }
+      g->links[n] = word;
+      if (word != 0u) g->bnodes.push_back(n);
+    }
+  }
+  g->n_solid = nsol;
+}
+
+}  // namespace
+
 extern "C" lbm_status lbm_geometry_create(int32_t nx, int32_t ny,
                                           const double *fibers,
                                           int32_t nfibers, double k1,
@@ -98,37 +141,7 @@ extern "C" lbm_status lbm_geometry_create(int32_t nx, int32_t ny,
       }
     }
 
-    // Link words of the fluid nodes.
-    int64_t nsol = 0;
-    for (int64_t y = 0; y < ny; ++y) {
-      for (int64_t x = 0; x < nx; ++x) {
-        const int64_t n = y * g->nx_pad + x;
-        if (g->solid[y * nx + x]) {
-          ++nsol;
-          continue;  // stays kSolidNode
-        }
-        uint32_t word = 0;
-        for (int j = 1; j < 9; ++j) {
-          const int64_t tx = x + kCx[j], ty = y + kCy[j];
-          uint32_t t;
-          if (tx < 0)
-            t = kInlet;  // the x-boundary rule wins on corner links
-          else if (tx >= nx)
-            t = kOutlet;
-          else if (ty < 0 || ty >= ny)
-            t = kWall;
-          else if (g->solid[ty * nx + tx]) {
-            const int64_t m = ty * g->nx_pad + tx;
-            t = (g->kab[m] != 0.0 || g->kbc[m] != 0.0) ? kCat : kInert;
-          } else
-            t = kFluid;
-          word |= t << (4 * (j - 1));
-        }
-        g->links[n] = word;
-        if (word != 0u) g->bnodes.push_back(n);
-      }
-    }
-    g->n_solid = nsol;
+    build_links(g);
   } catch (const std::bad_alloc &) {
     delete g;
     set_error("lbm_geometry_create: host allocation failed");
@@ -165,6 +178,43 @@ extern "C" lbm_status lbm_geometry_fields(const lbm_geometry *g,
       if (kab) kab[y * g->nx + x] = g->kab[n];
       if (kbc) kbc[y * g->nx + x] = g->kbc[n];
     }
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_geometry_set_rates(lbm_geometry *g,
+                                             const double *kab,
+                                             const double *kbc) {
+  if (!g) {
+    set_error("lbm_geometry_set_rates: geometry is NULL");
+    return LBM_EINVAL;
+  }
+  for (int k = 0; k < 2; ++k) {
+    const double *f = k == 0 ? kab : kbc;
+    if (!f) continue;
+    for (int64_t y = 0; y < g->ny; ++y)
+      for (int64_t x = 0; x < g->nx; ++x) {
+        const double v = f[y * g->nx + x];
+        if (!(v >= 0.0) || !std::isfinite(v) ||
+            (v != 0.0 && !g->solid[y * g->nx + x])) {
+          set_error("lbm_geometry_set_rates: rates must be finite, >= 0, "
+                    "and zero on fluid nodes");
+          return LBM_EINVAL;
+        }
+      }
+  }
+  try {
+    for (int64_t y = 0; y < g->ny; ++y)
+      for (int64_t x = 0; x < g->nx; ++x) {
+        const int64_t n = y * g->nx_pad + x;
+        if (kab) g->kab[n] = kab[y * g->nx + x];
+        if (kbc) g->kbc[n] = kbc[y * g->nx + x];
+      }
+    build_links(g);
+  } catch (const std::bad_alloc &) {
+    set_error("lbm_geometry_set_rates: host allocation failed");
+    return LBM_ENOMEM;
+  }
+  g->uploaded = false;   // the device copy is stale until the next upload
   return LBM_OK;
 }
 

@@ -73,6 +73,7 @@ _SIGS = {
     "lbm_geometry_destroy": (None, [_P]),
     "lbm_geometry_info": (ctypes.c_int, [_P, _P, _P]),
     "lbm_geometry_fields": (ctypes.c_int, [_P, _P, _P, _P]),
+    "lbm_geometry_set_rates": (ctypes.c_int, [_P, _P, _P]),
     "lbm_geometry_ws_bytes": (ctypes.c_size_t, [_P]),
     "lbm_geometry_upload": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
     "lbm_flow_ws_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),
@@ -184,8 +185,28 @@ class Geometry:
     def ws_bytes(self) -> int:
         return int(load().lbm_geometry_ws_bytes(self.handle))
 
+    def set_rates(self, kab=None, kbc=None):
+        """lbm_geometry_set_rates: per-node rate fields ([ny, nx] float64,
+        zero on fluid nodes; None keeps that rate).  Call upload() again
+        before the next solve (it rewrites the same device buffer)."""
+        arrs = []
+        for f in (kab, kbc):
+            arrs.append(None if f is None else np.ascontiguousarray(
+                np.asarray(f, dtype=np.float64).reshape(self.ny, self.nx)))
+        _check(load().lbm_geometry_set_rates(
+            self.handle, *[a.ctypes.data_as(_P) if a is not None else None
+                           for a in arrs]))
+        return self
+
     def upload(self, device="cuda", stream=None):
-        self.ws = _device_bytes(self.ws_bytes(), device)
+        import torch
+        nbytes = self.ws_bytes()
+        dev = torch.device(device)
+        if dev.type == "cuda" and dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        if not (self.ws is not None and self.ws.numel() == nbytes and
+                self.ws.device == dev):
+            self.ws = _device_bytes(nbytes, dev)
         _check(load().lbm_geometry_upload(self.handle,
                                           ctypes.c_void_p(self.ws.data_ptr()),
                                           self.ws.numel(),

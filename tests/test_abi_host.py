@@ -113,3 +113,31 @@ def test_workspace_sizes_scale_with_precision(lib):
     assert sizes["f16dev"] >= 2 * 27 * plane * 2
     assert sizes["f16dev"] < sizes["f32"] < sizes["f64"]
     assert lib.lbm_geometry_ws_bytes(g.handle) >= plane * (4 + 16)
+
+
+def test_set_rates_rebuilds_links_and_validates(lib):
+    """lbm_geometry_set_rates: per-node rates replace the raster's, the
+    catalytic / inert link types follow them, bad fields are refused and
+    leave the geometry unchanged."""
+    w = inputs.fiber_pair(20.0, 10.0)
+    g = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2)
+    solid, kab, kbc = g.fields()
+    new_ab = np.where(solid == 1, 0.0, 0.0)
+    ys, xs = np.nonzero(solid)
+    new_ab[ys[::2], xs[::2]] = 0.125        # every other solid node
+    g.set_rates(new_ab, None)
+    s2, a2, b2 = g.fields()
+    assert np.array_equal(s2, solid)
+    assert np.array_equal(a2, new_ab) and np.array_equal(b2, kbc)
+    for bad in (np.where(solid == 0, 0.1, 0.0),    # rate on a fluid node
+                np.full(solid.shape, -1.0) * solid,
+                np.where(solid == 1, np.nan, 0.0)):
+        with pytest.raises(lbm.LBMError) as e:
+            g.set_rates(bad, None)
+        assert e.value.status == lbm.LBM_EINVAL
+    _, a3, _ = g.fields()
+    assert np.array_equal(a3, new_ab)
+    # all rates zero: no catalytic links left
+    g.set_rates(np.zeros(solid.shape), np.zeros(solid.shape))
+    _, a4, b4 = g.fields()
+    assert not a4.any() and not b4.any()
