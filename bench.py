@@ -626,11 +626,14 @@ def run_adjoint(a):
 # ---------------------------------------------------------------------------
 def run_series(a):
     """Isolated A->B fiber (Da = 150, 1.5), A->B->C fiber pairs at xi = 2,
-    20, 100 and the side-by-side fiber (Da = 150), Pe = 1..30 where k < 1
-    and tau_c >= 0.52: 44 lattices of 300x300 and 1000x300.  Untimed: one FP64 flow per geometry.  Timed
+    20, 100, the side-by-side fiber (Da = 150), and membranes of six fibers
+    (three seeds; A->B at Da = 150, 1.5 and the A->B->C pair of membranes
+    at Da = 150), Pe = 1..30 where k < 1 and tau_c >= 0.52: 110 lattices
+    of 300x300 and 1000x300.  Untimed: one FP64 flow per geometry.  Timed
     on the host clock (the solves end synchronised): the launch-shape tuning
     and the batched ADR solves (two batches, 2 and 3 species) to a per-step
-    residual of 1e-7 or the 300000-step cap.  Reports solves/s, and per lattice the efficiency, the
+    residual of 2e-7 (FP32's floor at tau_c = 0.525 is ~1.1e-7) or the
+    300000-step cap.  Reports solves/s, and per lattice the efficiency, the
     collision-zone model's value and the production rate."""
     import torch
 
@@ -641,7 +644,7 @@ def run_series(a):
     flows = series.solve_flows(items)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rows, shapes = series.run(items, flows, precision=prec, tol=1e-7,
+    rows, shapes = series.run(items, flows, precision=prec, tol=2e-7,
                               max_steps=300000)
     torch.cuda.synchronize()
     t = time.perf_counter() - t0

@@ -208,6 +208,26 @@ def side_by_side_fiber(pe: float, da: float = 150.0, nx: int = 1000,
                     pe=pe, da1=da, da2=da, r_ref=r)
 
 
+def fiber_membrane(pe: float, da: float = 150.0, seed: int = 0,
+                   cascade: bool = False, n: int = 6, nx: int = 1000,
+                   ny: int = 300, r: int = 5, gap: float = 4.0) -> Workload:
+    """2D analogue of the membranes of Sec. IV (n randomly placed R = 5
+    fibers, seeded): one A->B membrane in the band x in [300, 400], and for
+    the cascade a B->C membrane in [450, 550] behind it; 1000 x 300 box."""
+    rng = SplitMix64(1000 + seed)
+    rows = place_fibers(rng, 300, 400, ny, n, r, r, gap, lambda _r: (1, 0.0))
+    ns = 2
+    if cascade:
+        rows += place_fibers(rng, 450, 550, ny, n, r, r, gap,
+                             lambda _r: (2, 0.0),
+                             [(f[0], f[1], f[2]) for f in rows])
+        ns = 3
+    kind = "cascade" if cascade else "AB"
+    return Workload(f"membrane_{kind}_seed{seed}_pe{pe:g}_da{da:g}", nx, ny,
+                    fiber_table(rows), ns, pe=pe, da1=da, da2=da,
+                    r_ref=float(r))
+
+
 def two_membrane_cascade(seed: int = 0, pe: float = 10.0, nx: int = 2048,
                          ny: int = 512, bands=((400, 700), (1000, 1300)),
                          per_band: int = 40, r: int = 8,

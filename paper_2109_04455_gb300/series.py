@@ -6,6 +6,10 @@
   whose surfaces are xi apart along the flow, and on one side-by-side R = 10
   fiber; the model of Sec. IV.B for fibers far apart is the product of the
   two single-fiber efficiencies.
+* Membranes of n = 6 random R = 5 fibers (2D analogue of Sec. IV, three
+  seeds): one A->B membrane (Da = 150, 1.5) against Eq. (eff_memb), and an
+  A->B membrane followed by a B->C membrane (Da = 150) against
+  Eq. (eff_ABC_memb), the square of the membrane efficiency.
 * Production rate of the final species (Appendix A).
 
 The inflow velocity u0 is fixed and Pe is set through D (so the flow depends
@@ -51,6 +55,16 @@ def model_efficiency(pe: float, da: float, r: float, width: float,
     return eps_coll * (1.0 - math.exp(-da * alpha * d * d / (2.0 * r * r)))
 
 
+def membrane_model(pe: float, da: float, r: float, width: float, n: int,
+                   shell: float = 0.5) -> float:
+    """Eq. (eff_memb): each of the n fibers of a membrane converts the share
+    eps of what the fibers before it left, so
+    eps_mem = sum_{i=1..n} eps (1 - eps)^(i-1) = 1 - (1 - eps)^n, with eps
+    the isolated-fiber model of Eq. (eps)."""
+    e = model_efficiency(pe, da, r, width, shell)
+    return 1.0 - (1.0 - e) ** n
+
+
 def production_rate(flux, ny: int, nspecies: int) -> float:
     """Appendix A: final product leaving the reactor per time step (per unit
     fiber length), N_final * ny with N_s the plane-averaged outflux."""
@@ -65,10 +79,18 @@ TAU_MIN = 0.52
 
 
 def workloads(pes=DEFAULT_PE, xis=(2.0, 20.0, 100.0),
-              das_isolated=(150.0, 1.5)):
+              das_isolated=(150.0, 1.5), membrane_seeds=(0, 1, 2)):
     """(geometry key, workload) pairs of the series with k < 1 and
     tau_c >= TAU_MIN."""
     out = []
+    for seed in membrane_seeds:
+        for da in das_isolated:
+            for pe in pes:
+                out.append((f"membrane_AB_seed{seed}",
+                            inputs.fiber_membrane(pe, da, seed)))
+        for pe in pes:
+            out.append((f"membrane_cascade_seed{seed}",
+                        inputs.fiber_membrane(pe, 150.0, seed, cascade=True)))
     for da in das_isolated:
         for pe in pes:
             out.append(("isolated_fiber", inputs.isolated_fiber(pe, da)))
@@ -135,6 +157,10 @@ def run(items=None, flows=None, precision: int = lbm.LBM_F32,
             if key == "isolated_fiber":
                 row["model_eps"] = model_efficiency(w.pe, w.da1, w.r_ref,
                                                     float(w.ny))
+            elif key.startswith("membrane_"):
+                n = w.fibers.shape[0] // (2 if ns == 3 else 1)
+                em = membrane_model(w.pe, w.da1, w.r_ref, float(w.ny), n)
+                row["model_eps"] = em if ns == 2 else em * em
             rows.append(row)
     # Eq. (eps_ABC) for the pairs: the square of one fiber's efficiency,
     # stated for fibers whose collision zones do not overlap (xi > 2d)

@@ -25,23 +25,27 @@ def _built():
 
 
 CASES = {
-    # name: (workload, flux plane just downstream of the catalysts)
-    "isolated_da150": (lambda: inputs.isolated_fiber(7.0, 150.0), 170),
-    "pair_xi2": (lambda: inputs.fiber_pair(2.0, 10.0), 330),
-    "side_by_side": (lambda: inputs.side_by_side_fiber(10.0), 330),
+    # name: (workload, flux plane just downstream of the catalysts, ADR
+    # steps: the cascade membrane needs B to reach its second band)
+    "isolated_da150": (lambda: inputs.isolated_fiber(7.0, 150.0), 170, NADR),
+    "pair_xi2": (lambda: inputs.fiber_pair(2.0, 10.0), 330, NADR),
+    "side_by_side": (lambda: inputs.side_by_side_fiber(10.0), 330, NADR),
+    "membrane_cascade": (lambda: inputs.fiber_membrane(10.0, 150.0, 1,
+                                                       cascade=True), 560,
+                         4000),
 }
 
 
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_series_geometry_f64_matches_oracle(name):
-    make, xp = CASES[name]
+    make, xp, nadr = CASES[name]
     w = make()
     ns = w.nspecies
     cin = list(w.c_in)[:ns]
     solid, kab, kbc = oracle.raster(w.nx, w.ny, w.fibers, w.k1, w.k2)
     _, ux, uy, _ = oracle.flow_run(solid, w.tau_flow, w.u0, NFLOW)
     prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, [w.tau_c] * ns, cin)
-    ref = prob.run(NADR, xp=xp)
+    ref = prob.run(nadr, xp=xp)
 
     geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
     gs, ga, gb = geom.fields()
@@ -52,7 +56,7 @@ def test_series_geometry_f64_matches_oracle(name):
     ug = u.cpu().numpy()[:, :, :w.nx]
     assert np.abs(ug[0] - ux).max() < 1e-12 and np.abs(ug[1] - uy).max() < 1e-12
     prm = lbm.adr_params(ns, w.tau_c, cin, precision=lbm.LBM_F64,
-                         max_steps=NADR, x_plane=xp)
+                         max_steps=nadr, x_plane=xp)
     conc, info = lbm.lbm_adr_solve(geom, prm, u)
     conc = conc.cpu().numpy()[:, :, :w.nx]
     rel = np.linalg.norm(conc - ref["conc"]) / np.linalg.norm(ref["conc"])
@@ -66,10 +70,11 @@ def test_series_geometry_f64_matches_oracle(name):
 def test_series_runner_matches_single_solves():
     """Two Pe values per geometry, fixed step count: every row of the
     batched runner equals lbm_adr_solve of the same lattice."""
-    items = series.workloads(pes=(10.0, 50.0), xis=(20.0,),
-                             das_isolated=(150.0,))
+    items = series.workloads(pes=(10.0, 30.0), xis=(20.0,),
+                             das_isolated=(150.0,), membrane_seeds=(0,))
     assert {k for k, _ in items} == {"isolated_fiber", "fiber_pair_xi20",
-                                     "side_by_side"}
+                                     "side_by_side", "membrane_AB_seed0",
+                                     "membrane_cascade_seed0"}
     flows = series.solve_flows(items, flow_tol=0.0, flow_max=2000)
     rows, shapes = series.run(items, flows, precision=lbm.LBM_F32, tol=0.0,
                               max_steps=2000, check_every=500)
@@ -86,4 +91,4 @@ def test_series_runner_matches_single_solves():
         assert abs(r["eps"] - info["eps"]) <= 1e-13
         assert r["production_rate"] == pytest.approx(
             info["flux"][w.nspecies - 1] * w.ny, rel=1e-12)
-        assert "model_eps" in r or key == "side_by_side"
+        assert ("model_eps" in r) == (key != "side_by_side")

@@ -63,3 +63,18 @@ def test_production_rate_is_outflux_times_width():
         pytest.approx(6.0)
     assert series.production_rate([0.9, 0.1, 0.0], 300, 2) == \
         pytest.approx(30.0)
+
+
+@pytest.mark.parametrize("n", [1, 6, 40])
+def test_membrane_model_is_the_fiber_by_fiber_sum(n):
+    # Eq. (eff_memb1): fiber i converts eps of what fibers 1..i-1 left
+    pe, da, r, l = 7.0, 150.0, 5.0, 300.0
+    e = series.model_efficiency(pe, da, r, l)
+    left, total = 1.0, 0.0
+    for _ in range(n):
+        total += e * left
+        left *= 1.0 - e
+    assert series.membrane_model(pe, da, r, l, n) == pytest.approx(
+        total, rel=1e-12)
+    if n == 1:
+        assert series.membrane_model(pe, da, r, l, 1) == pytest.approx(e)
