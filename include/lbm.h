@@ -238,6 +238,25 @@ lbm_status lbm_adr_solve(const lbm_geometry *g, const lbm_adr_params *p,
 /* paper's discrete scheme.                                                   */
 /* ------------------------------------------------------------------------ */
 
+/* Checkpoint / resume (no counterpart in the paper): the populations of the
+ * current state (and, for LBM_F16DEV, the half reference concentrations)
+ * are the whole state of a run.  lbm_adr_state_save copies them, behind a
+ * header (lattice size, species count, precision, step count), into the
+ * caller's host buffer of >= lbm_adr_state_bytes bytes (pinned or pageable)
+ * and waits for the copy; LBM_ENOMEM if the buffer is smaller.
+ * lbm_adr_state_load copies a saved state into a solver created for the same
+ * geometry size, species count and precision (LBM_EINVAL otherwise, nothing
+ * changed) and restores the step count, so that continuing from it gives
+ * bit for bit the run that was saved (the stochastic rounding of
+ * LBM_F16DEV is seeded by the step count).  The loaded state has no
+ * recorded concentrations: run with info before lbm_adr_conc or the
+ * adjoint. */
+size_t lbm_adr_state_bytes(const lbm_adr_solver *s);
+lbm_status lbm_adr_state_save(lbm_adr_solver *s, void *host, size_t bytes,
+                              void *stream);
+lbm_status lbm_adr_state_load(lbm_adr_solver *s, const void *host,
+                              size_t bytes, void *stream);
+
 /* Device bytes of the adjoint workspace (LBM_F64 or LBM_F32 precision). */
 size_t lbm_adr_adjoint_ws_bytes(const lbm_geometry *g, const lbm_adr_params *p);
 

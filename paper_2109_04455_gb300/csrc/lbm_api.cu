@@ -8,6 +8,7 @@
 #include <string>
 
 #include "lbm_kernels.cuh"
+#include "lbm_nvtx.h"
 
 namespace lbm {
 
@@ -173,6 +174,7 @@ extern "C" lbm_status lbm_flow_solve(const lbm_geometry *g,
                                      const lbm_flow_params *p, void *f_ws,
                                      size_t f_ws_bytes, void *u_out,
                                      void *stream, lbm_solve_info *info) {
+  NvtxRange nvtx_range("lbm_flow_solve");
   if (!g || !p || !f_ws || !u_out) {
     set_error("lbm_flow_solve: NULL argument");
     return LBM_EINVAL;
@@ -488,6 +490,7 @@ extern "C" void lbm_adr_destroy(lbm_adr_solver *s) {
 }
 
 extern "C" lbm_status lbm_adr_init(lbm_adr_solver *s, void *stream) {
+  NvtxRange nvtx_range("lbm_adr_init");
   if (!s) {
     set_error("lbm_adr_init: solver is NULL");
     return LBM_EINVAL;
@@ -526,6 +529,7 @@ static cudaError_t adr_step(lbm_adr_solver *s, int mode, cudaStream_t st) {
 
 extern "C" lbm_status lbm_adr_run(lbm_adr_solver *s, int64_t nsteps,
                                   void *stream, lbm_solve_info *info) {
+  NvtxRange nvtx_range("lbm_adr_run");
   if (!s || nsteps < 0 || (info && nsteps < 2)) {
     set_error("lbm_adr_run: need a solver, nsteps >= 0 (>= 2 with info)");
     return LBM_EINVAL;
@@ -600,10 +604,116 @@ extern "C" lbm_status lbm_adr_conc(lbm_adr_solver *s, void *conc_out,
   return LBM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// checkpoint / resume: the populations (and, for half storage, the reference
+// concentrations) of the current state are the whole state of a run
+// ---------------------------------------------------------------------------
+namespace {
+
+struct StateHeader {
+  uint64_t magic;
+  int32_t version, precision, nspecies, nx, ny, nx_pad;
+  int64_t steps;
+  uint64_t pop_bytes, ref_bytes;
+};
+constexpr uint64_t kStateMagic = 0x4c424d4144525354ull;  // "LBMADRST"
+
+size_t state_pop_bytes(const lbm_adr_solver *s) {
+  return static_cast<size_t>(s->p.nspecies) * 9 *
+         static_cast<size_t>(plane_of(s->g)) * store_bytes(s->p.precision);
+}
+size_t state_ref_bytes(const lbm_adr_solver *s) {
+  return s->p.precision == LBM_F16DEV
+             ? static_cast<size_t>(s->p.nspecies) *
+                   static_cast<size_t>(plane_of(s->g)) * sizeof(RefT)
+             : 0;
+}
+
+}  // namespace
+
+extern "C" size_t lbm_adr_state_bytes(const lbm_adr_solver *s) {
+  if (!s) return 0;
+  return sizeof(StateHeader) + state_pop_bytes(s) + state_ref_bytes(s);
+}
+
+extern "C" lbm_status lbm_adr_state_save(lbm_adr_solver *s, void *host,
+                                         size_t bytes, void *stream) {
+  NvtxRange nvtx_range("lbm_adr_state_save");
+  if (!s || !host) {
+    set_error("lbm_adr_state_save: NULL argument");
+    return LBM_EINVAL;
+  }
+  if (bytes < lbm_adr_state_bytes(s)) {
+    set_error("lbm_adr_state_save: host buffer smaller than lbm_adr_state_bytes");
+    return LBM_ENOMEM;
+  }
+  if (lbm_status bs = bind_device(s->buf[0], "lbm_adr_state_save")) return bs;
+  StateHeader h{};
+  h.magic = kStateMagic;
+  h.version = 1;
+  h.precision = s->p.precision;
+  h.nspecies = s->p.nspecies;
+  h.nx = s->g->nx;
+  h.ny = s->g->ny;
+  h.nx_pad = s->g->nx_pad;
+  h.steps = s->steps;
+  h.pop_bytes = state_pop_bytes(s);
+  h.ref_bytes = state_ref_bytes(s);
+  char *out = static_cast<char *>(host);
+  std::memcpy(out, &h, sizeof(h));
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(out + sizeof(h), s->buf[s->cur], h.pop_bytes,
+                                  cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && h.ref_bytes)
+    e = cudaMemcpyAsync(out + sizeof(h) + h.pop_bytes, s->rbuf[s->cur],
+                        h.ref_bytes, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_state_save", e);
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_adr_state_load(lbm_adr_solver *s, const void *host,
+                                         size_t bytes, void *stream) {
+  NvtxRange nvtx_range("lbm_adr_state_load");
+  if (!s || !host) {
+    set_error("lbm_adr_state_load: NULL argument");
+    return LBM_EINVAL;
+  }
+  StateHeader h{};
+  if (bytes < sizeof(h)) {
+    set_error("lbm_adr_state_load: buffer too small for a state header");
+    return LBM_EINVAL;
+  }
+  std::memcpy(&h, host, sizeof(h));
+  if (h.magic != kStateMagic || h.version != 1 ||
+      h.precision != s->p.precision || h.nspecies != s->p.nspecies ||
+      h.nx != s->g->nx || h.ny != s->g->ny || h.nx_pad != s->g->nx_pad ||
+      h.pop_bytes != state_pop_bytes(s) || h.ref_bytes != state_ref_bytes(s) ||
+      h.steps < 0 || bytes < sizeof(h) + h.pop_bytes + h.ref_bytes) {
+    set_error("lbm_adr_state_load: state does not match this solver "
+              "(lattice, species count or precision) or is truncated");
+    return LBM_EINVAL;
+  }
+  if (lbm_status bs = bind_device(s->buf[0], "lbm_adr_state_load")) return bs;
+  const char *in = static_cast<const char *>(host);
+  cudaStream_t st = as_stream(stream);
+  cudaError_t e = cudaMemcpyAsync(s->buf[s->cur], in + sizeof(h), h.pop_bytes,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && h.ref_bytes)
+    e = cudaMemcpyAsync(s->rbuf[s->cur], in + sizeof(h) + h.pop_bytes,
+                        h.ref_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_state_load", e);
+  s->steps = h.steps;
+  s->has_check = false;   // no concentrations recorded for this state yet
+  return LBM_OK;
+}
+
 extern "C" lbm_status lbm_adr_solve(const lbm_geometry *g,
                                     const lbm_adr_params *p, const void *u,
                                     void *ws, size_t ws_bytes, void *conc_out,
                                     void *stream, lbm_solve_info *info) {
+  NvtxRange nvtx_range("lbm_adr_solve");
   if (!p || p->max_steps < 2 || (p->tol > 0 && p->check_every < 2)) {
     set_error("lbm_adr_solve: need max_steps >= 2 and check_every >= 2");
     return LBM_EINVAL;
@@ -695,6 +805,7 @@ extern "C" lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps,
                                       size_t ws_bytes, void *dkab, void *dkbc,
                                       void *dw, void *stream,
                                       lbm_solve_info *info) {
+  NvtxRange nvtx_range("lbm_adr_adjoint");
   if (!s || !ws || !dkab || !dkbc) {
     set_error("lbm_adr_adjoint: NULL argument");
     return LBM_EINVAL;

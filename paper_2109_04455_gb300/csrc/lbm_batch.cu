@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "lbm_kernels.cuh"
+#include "lbm_nvtx.h"
 
 namespace lbm {
 namespace batch {
@@ -571,6 +572,7 @@ extern "C" void lbm_batch_destroy(lbm_batch *b) {
 
 extern "C" lbm_status lbm_batch_tune(lbm_batch *b, void *stream,
                                      int32_t *tile, int32_t *grid) {
+  NvtxRange nvtx_range("lbm_batch_tune");
   if (!b) {
     set_error("lbm_batch_tune: batch is NULL");
     return LBM_EINVAL;
@@ -632,6 +634,7 @@ extern "C" lbm_status lbm_batch_tune(lbm_batch *b, void *stream,
 
 extern "C" lbm_status lbm_batch_solve(lbm_batch *b, void *stream,
                                       lbm_solve_info *infos) {
+  NvtxRange nvtx_range("lbm_batch_solve");
   if (!b || !infos) {
     set_error("lbm_batch_solve: NULL argument");
     return LBM_EINVAL;

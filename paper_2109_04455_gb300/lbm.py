@@ -74,6 +74,9 @@ _SIGS = {
     "lbm_geometry_info": (ctypes.c_int, [_P, _P, _P]),
     "lbm_geometry_fields": (ctypes.c_int, [_P, _P, _P, _P]),
     "lbm_geometry_set_rates": (ctypes.c_int, [_P, _P, _P]),
+    "lbm_adr_state_bytes": (ctypes.c_size_t, [_P]),
+    "lbm_adr_state_save": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
+    "lbm_adr_state_load": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
     "lbm_geometry_ws_bytes": (ctypes.c_size_t, [_P]),
     "lbm_geometry_upload": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
     "lbm_flow_ws_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),
@@ -340,6 +343,22 @@ class ADRSolver:
                                  not raise_not_converged):
             _check(st)
         return dkab, dkbc, dw, info.as_dict()
+
+    def state_save(self, stream=None) -> np.ndarray:
+        """lbm_adr_state_save into a new host byte array (the checkpoint)."""
+        lib = load()
+        n = int(lib.lbm_adr_state_bytes(self.handle))
+        buf = np.empty(n, dtype=np.uint8)
+        _check(lib.lbm_adr_state_save(self.handle, buf.ctypes.data_as(_P), n,
+                                      _stream_ptr(stream)))
+        return buf
+
+    def state_load(self, buf, stream=None):
+        """lbm_adr_state_load from a checkpoint made by state_save."""
+        b = np.ascontiguousarray(np.asarray(buf, dtype=np.uint8))
+        _check(load().lbm_adr_state_load(self.handle, b.ctypes.data_as(_P),
+                                         b.size, _stream_ptr(stream)))
+        return self
 
     def solve(self, tol: float, check_every: int, max_steps: int,
               stream=None):
