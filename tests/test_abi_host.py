@@ -90,6 +90,21 @@ def test_argument_errors_are_status_codes(lib):
         lbm.lbm_efficiency([0.0, 0.0, 0.0], 3)
     with pytest.raises(lbm.LBMError):
         lbm.lbm_efficiency([1.0, 0.0, 0.0], 1)
+    # lattice height limit (one grid row of blocks per lattice row)
+    st = lib.lbm_geometry_create(8, 65536, None, 0, 0.0, 0.0, ctypes.byref(h))
+    assert st == lbm.LBM_EINVAL
+    g1 = lbm.Geometry(8, 65535, np.zeros((0, 6)), 0.0, 0.0)
+    assert g1.nx_pad == 32 and g1.n_solid == 0
+    g1.close()
+    # negative rates, unknown ADR flag bits
+    st = lib.lbm_geometry_create(10, 10, None, 0, -0.1, 0.0, ctypes.byref(h))
+    assert st == lbm.LBM_EINVAL
+    prm = lbm.adr_params(3, 0.62, precision=lbm.LBM_F32, flags=1 << 5)
+    assert lib.lbm_adr_ws_bytes(g.handle, ctypes.byref(prm)) == 0
+    prm = lbm.adr_params(3, 0.62, precision=lbm.LBM_F32,
+                         flags=lbm.LBM_ADR_NODEWISE |
+                         lbm.LBM_ADR_INLET_ABB_ALL)
+    assert lib.lbm_adr_ws_bytes(g.handle, ctypes.byref(prm)) > 0
 
 
 def test_efficiency_host_call(lib):
