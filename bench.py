@@ -140,6 +140,16 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
+# FP64 arithmetic peak of the part: 2 double FMA instructions per clock per
+# SM (ncu: the FP64 pipe of the FP64 step was 86% busy at 1.71 double
+# instructions per SM clock) x 152 SMs x 2.07 GHz x 2 flops per FMA
+FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
+# algorithmic double flops of one FP64 interior node update with the E table:
+# per species 8 additions for C and, per population, C E_i - g and
+# g + omega (...) as two FMAs (4 flops)
+FP64_FLOPS_PER_NODE = SPECIES * (8 + 9 * 4)
+
+
 def _peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -194,9 +204,9 @@ def _ncu_traffic(precision: str, units_per_launch: int):
 def _algorithmic_bytes(geom, w, precision):
     """Bytes one ADR step must move: per fluid node 3 species x 9
     populations read + written, the velocity (2 values) and the link word
-    (half storage: also each species' float reference, read + written); per
-    solid node its link word; the rates of each catalytic link (two
-    doubles)."""
+    (half storage: also each species' half reference, read + written; FP64:
+    the nine equilibrium factors instead of the velocity); per solid node
+    its link word; the rates of each catalytic link (two doubles)."""
     import numpy as np
     import torch
     es = {"f32": 4, "f16dev": 2, "f64": 8}[precision]
@@ -212,6 +222,8 @@ def _algorithmic_bytes(geom, w, precision):
     per_fluid = SPECIES * 9 * 2 * es + 2 * ue + 4
     if precision == "f16dev":
         per_fluid += SPECIES * 2 * 2   # per-node half reference, read + written
+    if precision == "f64":
+        per_fluid += 9 * 8 - 2 * ue    # the E_i(u) table is read instead of u
     total = n_fluid * per_fluid + n_solid * 4 + ncat * 16
     return total, n_fluid, per_fluid
 
@@ -440,10 +452,21 @@ def run_gpu(a):
                       "f64": "f64"}[a.precision],
             "data": "synthetic (seeded fiber geometry)",
             "config": _config(a, w),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak,
+            "roofline": ({"bound": "hbm", "achieved": achieved,
+                          "peak": peak, "unit": "GB/s",
+                          "frac": achieved / peak,
+                          "peak_kind": f"{peak_kind} (copy bandwidth)"}
+                         if a.precision != "f64" else
+                         {"bound": "alu",
+                          "achieved": FP64_FLOPS_PER_NODE * n_fluid /
+                          step_launch_s / 1e12,
+                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": FP64_FLOPS_PER_NODE * n_fluid /
+                          step_launch_s / 1e12 / FP64_PEAK_TFLOPS,
+                          "peak_kind": "derived: 2 FP64 FMA/clk/SM x 152 "
+                                       "SMs x 2.07 GHz",
+                          "hbm_gbs": achieved}) | {
                          "traffic": traffic,
-                         "peak_kind": f"{peak_kind} (copy bandwidth)",
                          "kernel": ("adr_bulk_pair_kernel<3 species,step> "
                                     "(f16dev)" if a.precision == "f16dev" else
                                     f"adr_bulk_kernel<{a.precision},3 species,step>"),

@@ -15,4 +15,12 @@ template cudaError_t launch_adjoint<PrecF64>(int, int, const AdjArgs &,
 template cudaError_t launch_adjoint_grad<PrecF64>(
     int, const AdjArgs &, const long long *, long long, const void *, double *,
     double *, const int32_t *, double *, double, double, cudaStream_t);
+
+cudaError_t launch_eq_table(const double *u, long long plane, double *etab,
+                            cudaStream_t st) {
+  const long long blocks = (plane + 255) / 256;
+  eq_table_kernel<double><<<static_cast<unsigned>(blocks), 256, 0, st>>>(
+      u, plane, etab);
+  return cudaGetLastError();
+}
 }  // namespace lbm

@@ -316,7 +316,7 @@ struct lbm_adr_solver {
 };
 
 struct AdrLayout {
-  size_t buf, cprev, partials, scratch, result, ref, total;
+  size_t buf, cprev, partials, scratch, result, ref, etab, total;
 };
 
 static AdrLayout adr_layout(const lbm_geometry *g, const lbm_adr_params *p) {
@@ -333,7 +333,10 @@ static AdrLayout adr_layout(const lbm_geometry *g, const lbm_adr_params *p) {
   l.result = align256(64 * 8);
   // half storage: per-node reference concentrations of both buffers
   l.ref = p->precision == LBM_F16DEV ? align256(ns * pl * sizeof(RefT)) : 0;
-  l.total = 2 * l.buf + l.cprev + l.partials + l.scratch + l.result + 2 * l.ref;
+  // FP64: the equilibrium factors E_i(u) of the frozen velocity [9][plane]
+  l.etab = p->precision == LBM_F64 ? align256(9 * pl * sizeof(double)) : 0;
+  l.total = 2 * l.buf + l.cprev + l.partials + l.scratch + l.result +
+            2 * l.ref + l.etab;
   return l;
 }
 
@@ -433,6 +436,10 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
   s->scratch = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials);
   s->result = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials +
                                          l.scratch);
+  double *etab = nullptr;
+  if (l.etab)
+    etab = reinterpret_cast<double *>(b + 2 * l.buf + l.cprev + l.partials +
+                                      l.scratch + l.result + 2 * l.ref);
   if (l.ref) {
     char *rb = b + 2 * l.buf + l.cprev + l.partials + l.scratch + l.result;
     s->rbuf[0] = reinterpret_cast<RefT *>(rb);
@@ -445,6 +452,7 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
   a.kab = g->d_kab;
   a.kbc = g->d_kbc;
   a.u = u;
+  a.etab = etab;
   a.cprev = s->cprev;
   a.partials = s->partials;
   a.bnodes = g->d_bnodes;
@@ -501,6 +509,9 @@ extern "C" lbm_status lbm_adr_init(lbm_adr_solver *s, void *stream) {
   cudaError_t e = cudaMemsetAsync(s->buf[0], 0, 2 * l.buf + l.cprev, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->result, 0, 16 * sizeof(double), st);
   if (e == cudaSuccess && l.ref) e = cudaMemsetAsync(s->rbuf[0], 0, 2 * l.ref, st);
+  if (e == cudaSuccess && s->a.etab)
+    e = launch_eq_table(static_cast<const double *>(s->a.u), plane_of(s->g),
+                        const_cast<double *>(s->a.etab), st);
   if (e != cudaSuccess) return cuda_fail("lbm_adr_init", e);
   AdrArgs a = s->a;
   a.src = nullptr;
@@ -871,6 +882,7 @@ extern "C" lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps,
   a.kab = g->d_kab;
   a.kbc = g->d_kbc;
   a.u = s->a.u;
+  a.etab = s->a.etab;
   a.partials = partials;
   a.plane = plane_of(g);
   a.nx = g->nx;

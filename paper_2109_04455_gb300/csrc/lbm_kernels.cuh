@@ -203,9 +203,15 @@ struct AdrArgs {
   // populations (the stored value is g - w_i R of its node)
   const RefT *rsrc;
   RefT *rdst;
+  // FP64: equilibrium factors E_i(u) [9][plane] of the frozen velocity,
+  // filled once by eq_table_kernel (nullptr: computed per node and step;
+  // the FP64 step is bound by this part's FP64 pipe, and the table takes
+  // about a third of its double operations away)
+  const double *etab;
 };
 
 enum AdrMode { kAdrStep = 0, kAdrCheck = 1, kAdrInit = 2 };
+
 
 // value added back to the stored population (s, i) of node m (half storage
 // only: w_i times the node's reference concentration)
@@ -245,6 +251,49 @@ __device__ __forceinline__ void eq_factors(T ux, T uy, T (&E)[9]) {
     const T cu = T(cx(i)) * ux + T(cy(i)) * uy;
     E[i] = Lattice<T>::w(i) * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
   }
+}
+// The double version is written with explicit roundings: the FP64 step reads
+// E from a table that eq_table_kernel fills once per solver, while boundary
+// nodes and the batch kernel compute it in place, and all of them must get
+// the same bits.
+template <>
+__device__ __forceinline__ void eq_factors<double>(double ux, double uy,
+                                                   double (&E)[9]) {
+  const double base = __fma_rn(-1.5, __fma_rn(ux, ux, __dmul_rn(uy, uy)), 1.0);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const double cu = __dadd_rn(double(cx(i)) * ux, double(cy(i)) * uy);
+    E[i] = __dmul_rn(Lattice<double>::w(i),
+                     __fma_rn(__dmul_rn(4.5, cu), cu, __fma_rn(3.0, cu, base)));
+  }
+}
+
+// equilibrium factors of node n: from the FP64 table when there is one
+template <class P>
+__device__ __forceinline__ void adr_eq(const AdrArgs &a, long long n,
+                                       typename P::T (&E)[9]) {
+  using T = typename P::T;
+  if constexpr (sizeof(T) == 8) {
+    if (a.etab != nullptr) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) E[i] = a.etab[(long long)i * a.plane + n];
+      return;
+    }
+  }
+  const T *__restrict__ U = static_cast<const T *>(a.u);
+  eq_factors<T>(U[n], U[a.plane + n], E);
+}
+
+// E_i(u) of every node of the lattice into etab [9][plane] (FP64 only)
+template <typename T>
+__global__ void __launch_bounds__(256)
+    eq_table_kernel(const T *u, long long plane, T *etab) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= plane) return;
+  T E[9];
+  eq_factors<T>(u[n], u[plane + n], E);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) etab[(long long)i * plane + n] = E[i];
 }
 
 // The species are updated one after the other (A, then B, then C): the
@@ -361,10 +410,9 @@ __device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
   using T = typename P::T;
   const long long plane = a.plane;
   S *__restrict__ dst = static_cast<S *>(a.dst);
-  const T *__restrict__ U = static_cast<const T *>(a.u);
   const long long np = (long long)a.nx_pad;
   T E[9];
-  eq_factors<T>(U[n], U[plane + n], E);
+  adr_eq<P>(a, n, E);
   T C[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -421,7 +469,6 @@ __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
   const long long np = a.nx_pad, plane = a.plane;
   const S *__restrict__ src = static_cast<const S *>(a.src);
   S *__restrict__ dst = static_cast<S *>(a.dst);
-  const T *__restrict__ U = static_cast<const T *>(a.u);
   T g[NS][9];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -440,7 +487,7 @@ __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
     for (int s = 0; s < NS; ++s) prev[s] = cp[s * plane + n];
   }
   T E[9];
-  eq_factors<T>(U[n], U[plane + n], E);
+  adr_eq<P>(a, n, E);
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     T c = T(0);
@@ -587,6 +634,7 @@ struct AdjArgs {
   const uint32_t *links;
   const double *kab, *kbc;
   const void *u;            // T [2][plane]
+  const double *etab;       // FP64: E_i(u) [9][plane] of the forward solver
   double *partials;         // [rows][2]  (check iterations)
   long long plane;
   int nx, ny, nx_pad, xp;
@@ -643,9 +691,14 @@ __global__ void __launch_bounds__(kBlockX) adj_kernel(const AdjArgs a) {
   const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
   T acc[2] = {T(0), T(0)};
   if (lw != kSolidNode) {
-    const T *U = static_cast<const T *>(a.u);
     T E[9];
-    eq_factors<T>(U[n], U[plane + n], E);
+    if (sizeof(T) == 8 && a.etab != nullptr) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) E[i] = T(a.etab[(long long)i * plane + n]);
+    } else {
+      const T *U = static_cast<const T *>(a.u);
+      eq_factors<T>(U[n], U[plane + n], E);
+    }
     T mu[NS][9];
 #pragma unroll
     for (int s = 0; s < NS; ++s) adj_gather<T>(a, s, lw, n, x, mu[s]);
@@ -912,6 +965,10 @@ template <class P>
 cudaError_t launch_flow(int mode, const FlowArgs &a, dim3 grid, cudaStream_t st);
 template <class P>
 cudaError_t launch_adjoint(int ns, int mode, const AdjArgs &a, cudaStream_t st);
+// FP64 equilibrium-factor table of a velocity field (defined with the FP64
+// kernels)
+cudaError_t launch_eq_table(const double *u, long long plane, double *etab,
+                            cudaStream_t st);
 template <class P>
 cudaError_t launch_adjoint_grad(int ns, const AdjArgs &a, const long long *bnodes,
                                 long long nbnd, const void *conc, double *dkab,
