@@ -506,7 +506,7 @@ def run_sweep(a):
     lattices, and stopping there leaves the efficiency off by up to 1e-2),
     or with --sweep-tol to a residual tolerance;
     batched (one lbm_batch for all, FP32 and FP16 storage) against one
-    lbm_adr_solve per instance in FP64.  Reports solves/s and the largest
+    lbm_adr_solve per instance in FP64 and in FP32.  Reports solves/s and the largest
     efficiency difference to FP64."""
     import torch
 
@@ -554,6 +554,18 @@ def run_sweep(a):
                              "converged": sum(r["converged"] for r in ref),
                              "steps": sum(r["steps"] for r in ref)}}
     u32 = [u.float() for u in u64]
+    # unbatched FP32: the gain of batching alone, at the same precision
+    p32 = params(lbm.LBM_F32, a.sweep_tol)
+    torch.cuda.synchronize()
+    ev0.record()
+    ref32 = [lbm.lbm_adr_solve(g, p, u, want_conc=False)[1]
+             for g, p, u in zip(geoms, p32, u32)]
+    ev1.record()
+    torch.cuda.synchronize()
+    t32 = ev0.elapsed_time(ev1) * 1e-3
+    out["f32_unbatched"] = {"solves_per_s": len(ws) / t32, "seconds": t32,
+                            "speedup_vs_f64": t64 / t32,
+                            "steps": sum(r["steps"] for r in ref32)}
     # with a tolerance: FP64 to tol * 1e-3, FP32 to tol, FP16 (stochastic
     # rounding: a per-step residual floor of a few 1e-6) to max(tol, 1e-5)
     tols = {lbm.LBM_F32: a.sweep_tol,
@@ -572,6 +584,7 @@ def run_sweep(a):
         de = max(abs(i["eps"] - r["eps"]) for i, r in zip(infos, ref))
         out[name] = {"solves_per_s": len(ws) / t, "seconds": t, "tol": tol,
                      "speedup_vs_f64": t64 / t,
+                     "speedup_vs_f32_unbatched": t32 / t,
                      "max_abs_eps_err_vs_f64": de,
                      "converged": sum(i["converged"] for i in infos),
                      "steps": sum(i["steps"] for i in infos),

@@ -88,6 +88,26 @@ __device__ __forceinline__ __half round_half(float v, uint32_t h, int k) {
   return __float2half_rn(v);
 #endif
 }
+// The two nodes of a pair (lo: even x, hi: odd x) at store index k =
+// 9 s + i.  LBM_F16_SR_HW = 1: one cvt.rs instruction rounds both
+// stochastically with 32 random bits from the same hash; otherwise
+// round_half above, element by element.
+#ifndef LBM_F16_SR_HW
+#define LBM_F16_SR_HW 0
+#endif
+__device__ __forceinline__ __half2 round_pair(float lo, float hi, uint32_t h,
+                                              int k) {
+#if LBM_F16_SR && LBM_F16_SR_HW
+  const uint32_t r = h * (0x9E3779B1u + 2u * static_cast<uint32_t>(k));
+  uint32_t d;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+  __half2 out;
+  memcpy(&out, &d, sizeof(d));
+  return out;
+#else
+  return __halves2half2(round_half(lo, h, k), round_half(hi, h, 27 + k));
+#endif
+}
 }  // namespace f16
 
 template <int NS, int MODE>
@@ -116,7 +136,7 @@ __device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long lon
   float E[9];
   f16::eq(U[n], U[plane + n], E);
   const uint32_t h = f16::pair_hash(n >> 1, a.step);
-  const int kn = static_cast<int>(n & 1) * 27;   // second node of its pair
+  const bool odd = (n & 1) != 0;   // second node of its pair
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     const float cs = f16::sum9(g[s]);
@@ -124,9 +144,14 @@ __device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long lon
     const float cqs = __fmul_rn(ref_round(c), f16::kUp);
     a.rdst[s * plane + n] = __float2half_rn(c);
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-      dst[(long long)(s * 9 + i) * plane + n] = f16::round_half(
-          f16::push(i, g[s][i], cs, E[i], a.fomega[s], cqs), h, kn + s * 9 + i);
+    for (int i = 0; i < 9; ++i) {
+      // rounded as one half of its pair, with the pair's random bits
+      const float v = f16::push(i, g[s][i], cs, E[i], a.fomega[s], cqs);
+      const __half2 r2 = f16::round_pair(odd ? 0.0f : v, odd ? v : 0.0f, h,
+                                         s * 9 + i);
+      dst[(long long)(s * 9 + i) * plane + n] = odd ? __high2half(r2)
+                                                    : __low2half(r2);
+    }
     if (MODE == kAdrCheck) {
       acc[2 * s] += fabsf(c - prev[s]);
       acc[2 * s + 1] += fabsf(c);
@@ -243,17 +268,20 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
       if (in0 && in1) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-          *reinterpret_cast<__half2 *>(o + (long long)i * plane) = __halves2half2(
-              f16::round_half(f16::push(i, g0[i], cs0, E0[i], om, cq0), hp, s * 9 + i),
-              f16::round_half(f16::push(i, g1[i], cs1, E1[i], om, cq1), hp, 27 + s * 9 + i));
+          *reinterpret_cast<__half2 *>(o + (long long)i * plane) = f16::round_pair(
+              f16::push(i, g0[i], cs0, E0[i], om, cq0),
+              f16::push(i, g1[i], cs1, E1[i], om, cq1), hp, s * 9 + i);
         *reinterpret_cast<__half2 *>(ro) = __floats2half2_rn(c0, c1);
         if (MODE == kAdrCheck) *reinterpret_cast<float2 *>(co) = make_float2(c0, c1);
       } else {
         // one interior node: the other belongs to the boundary kernel
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-          if (in0) o[(long long)i * plane] = f16::round_half(f16::push(i, g0[i], cs0, E0[i], om, cq0), hp, s * 9 + i);
-          if (in1) o[(long long)i * plane + 1] = f16::round_half(f16::push(i, g1[i], cs1, E1[i], om, cq1), hp, 27 + s * 9 + i);
+          const __half2 r2 = f16::round_pair(
+              in0 ? f16::push(i, g0[i], cs0, E0[i], om, cq0) : 0.0f,
+              in1 ? f16::push(i, g1[i], cs1, E1[i], om, cq1) : 0.0f, hp, s * 9 + i);
+          if (in0) o[(long long)i * plane] = __low2half(r2);
+          if (in1) o[(long long)i * plane + 1] = __high2half(r2);
         }
         if (in0) ro[0] = __float2half_rn(c0);
         if (in1) ro[1] = __float2half_rn(c1);
