@@ -51,38 +51,6 @@ __device__ __forceinline__ float push(int i, float g, float cs, float e, float o
   const float post = __fmaf_rn(om, __fmaf_rn(cs, e, -g), g);
   return __fmaf_rn(-w(i), cqs, post);
 }
-// The same value regrouped as (1 - om) G + (om Cs E_i - w_i cqs), with the
-// per-species factors om Cs, 1 - om and w cqs (three weights) taken once:
-// two FMAs per population instead of three (LBM_F16_PUSH2 = 1).
-#ifndef LBM_F16_PUSH2
-#define LBM_F16_PUSH2 0
-#endif
-struct PushCoef {
-  float omc, a, b[3];
-};
-__device__ __forceinline__ PushCoef push_coef(float cs, float om, float cqs) {
-  PushCoef p;
-  p.omc = __fsub_rn(1.0f, om);
-  p.a = __fmul_rn(om, cs);
-  p.b[0] = __fmul_rn(w(0), cqs);
-  p.b[1] = __fmul_rn(w(1), cqs);
-  p.b[2] = __fmul_rn(w(5), cqs);
-  return p;
-}
-__device__ __forceinline__ float push_any(int i, float g, float cs, float e,
-                                          float om, float cqs,
-                                          const PushCoef &p) {
-#if LBM_F16_PUSH2
-  (void)cs;
-  (void)om;
-  (void)cqs;
-  const float b = p.b[i == 0 ? 0 : (i < 5 ? 1 : 2)];
-  return __fmaf_rn(p.omc, g, __fmaf_rn(p.a, e, -b));
-#else
-  (void)p;
-  return push(i, g, cs, e, om, cqs);
-#endif
-}
 
 // Rounding of a scaled population to half.  LBM_F16_SR = 1 (default):
 // stochastic rounding.  The float's 13 mantissa bits below half precision
@@ -179,11 +147,10 @@ __device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long lon
     const float c = __fmul_rn(cs, f16::kDown);
     const float cqs = __fmul_rn(ref_round(c), f16::kUp);
     a.rdst[s * plane + n] = __float2half_rn(c);
-    const f16::PushCoef pc = f16::push_coef(cs, a.fomega[s], cqs);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       // rounded as one half of its pair, with the pair's random bits
-      const float v = f16::push_any(i, g[s][i], cs, E[i], a.fomega[s], cqs, pc);
+      const float v = f16::push(i, g[s][i], cs, E[i], a.fomega[s], cqs);
       const __half2 r2 = f16::round_pair(odd ? 0.0f : v, odd ? v : 0.0f, h,
                                          s * 9 + i);
       dst[(long long)(s * 9 + i) * plane + n] = odd ? __high2half(r2)
@@ -299,8 +266,6 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
       const float cq0 = __fmul_rn(ref_round(c0), f16::kUp);
       const float cq1 = __fmul_rn(ref_round(c1), f16::kUp);
       const float om = a.fomega[s];
-      const f16::PushCoef pc0 = f16::push_coef(cs0, om, cq0);
-      const f16::PushCoef pc1 = f16::push_coef(cs1, om, cq1);
       __half *o = dst + (long long)s * 9 * plane + n0;
       __half *ro = a.rdst + (long long)s * plane + n0;
       float *co = cp + s * plane + n0;
@@ -308,8 +273,8 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
 #pragma unroll
         for (int i = 0; i < 9; ++i)
           *reinterpret_cast<__half2 *>(o + (long long)i * plane) = f16::round_pair(
-              f16::push_any(i, g0[i], cs0, E0[i], om, cq0, pc0),
-              f16::push_any(i, g1[i], cs1, E1[i], om, cq1, pc1), hp, s * 9 + i);
+              f16::push(i, g0[i], cs0, E0[i], om, cq0),
+              f16::push(i, g1[i], cs1, E1[i], om, cq1), hp, s * 9 + i);
         *reinterpret_cast<__half2 *>(ro) = __floats2half2_rn(c0, c1);
         if (MODE == kAdrCheck) *reinterpret_cast<float2 *>(co) = make_float2(c0, c1);
       } else {
@@ -317,8 +282,8 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           const __half2 r2 = f16::round_pair(
-              in0 ? f16::push_any(i, g0[i], cs0, E0[i], om, cq0, pc0) : 0.0f,
-              in1 ? f16::push_any(i, g1[i], cs1, E1[i], om, cq1, pc1) : 0.0f, hp, s * 9 + i);
+              in0 ? f16::push(i, g0[i], cs0, E0[i], om, cq0) : 0.0f,
+              in1 ? f16::push(i, g1[i], cs1, E1[i], om, cq1) : 0.0f, hp, s * 9 + i);
           if (in0) o[(long long)i * plane] = __low2half(r2);
           if (in1) o[(long long)i * plane + 1] = __high2half(r2);
         }
