@@ -17,7 +17,7 @@ CU_SOURCES = ["lbm_api.cu", "kernels_f64.cu", "kernels_f32.cu",
               "kernels_f16dev.cu", "lbm_batch.cu"]
 CPP_SOURCES = ["geometry.cpp"]
 HEADERS = ["lbm_internal.h", "lbm_kernels.cuh", "lbm_launch_impl.cuh",
-           "lbm_tma.cuh", "lbm_f16.cuh", "lbm_nvtx.h"]
+           "lbm_tma.cuh", "lbm_f16.cuh", "lbm_nvtx.h", "lbm_adjoint.cuh"]
 
 
 def _cu_cmd(src, obj):
