@@ -244,6 +244,29 @@ def test_gaussian_hill_vs_analytic_profile(u, t):
     assert err < 2e-2
 
 
+@pytest.mark.parametrize("u,t", [((0.0, 0.0), 50), ((0.0, 0.0), 100),
+                                 ((0.0, 0.0), 400), ((0.1, 0.1), 50),
+                                 ((0.1, 0.1), 100), ((0.1, 0.1), 400)])
+def test_gaussian_hill_sigma4_vs_analytic_profile(u, t):
+    """Appendix C at sigma0 = 4 (a hill the lattice resolves): with tau = 1
+    (D = 1/6) the profile follows the continuum solution
+    C = s0^2/(s0^2 + 2Dt) exp(-|x - x0 - ut|^2 / (2(s0^2 + 2Dt))) to 1e-3
+    of the peak."""
+    n = 160
+    prob, c0, x, y = _gauss_problem(n, 4.0, 1.0, u)
+    g = prob.init(c0[None])
+    prob.steps(g, t)
+    c = prob.conc(g)[0]
+    s2 = 16.0 + 2 * (1.0 / 6.0) * t
+    ana = np.zeros_like(c)
+    for ix in (-1, 0, 1):
+        for iy in (-1, 0, 1):
+            dx = x - n / 2 - u[0] * t + ix * n
+            dy = y - n / 2 - u[1] * t + iy * n
+            ana += (16.0 / s2) * np.exp(-(dx**2 + dy**2) / (2 * s2))
+    assert np.abs(c - ana).max() / ana.max() < 1e-3
+
+
 # ---------------------------------------------------------------------------
 # p4: flow lattice
 # ---------------------------------------------------------------------------
@@ -354,6 +377,207 @@ def test_species_sum_invariant_cascade(variant):
     # and the reaction really happened
     c = p3.conc(g3)
     assert c[1].max() > 1e-3 and c[2].max() > 1e-4
+
+
+# ---------------------------------------------------------------------------
+# p6: the outflux of Sec. III.A.3 and steady flux conservation.  None of these
+# pins calls the oracle's flux routine to make its expected value: they use
+# the first moments of the BGK collision, the boundary rules of Eq. (BC)
+# inverted on the pre-collision steady state, and the streaming map.
+# ---------------------------------------------------------------------------
+PLUS, MINUS = [1, 5, 8], [3, 6, 7]   # directions with c_ix = +1 and -1
+
+
+def _source_x_moment(ns, kab, kbc, solid, c, xp, y):
+    """sum_i c_ix Q_{s,i} at fluid node (xp, y) for the link-wise source of
+    Eq. (source_lbm): links into a solid node t carry Q_A = -k_AB(t) w C_A,
+    Q_B = +k_AB w C_A - k_BC w C_B, Q_C = +k_BC w C_B (walls carry none)."""
+    ny, nx = solid.shape
+    q = np.zeros(ns)
+    for i in range(1, 9):
+        tx, ty = xp + CX[i], y + CY[i]
+        if not (0 <= ty < ny and 0 <= tx < nx) or not solid[ty, tx]:
+            continue
+        ra = kab[ty, tx] * W[i] * c[0]
+        rb = kbc[ty, tx] * W[i] * c[1] if ns >= 3 else 0.0
+        q[0] -= CX[i] * ra
+        if ns >= 2:
+            q[1] += CX[i] * (ra - rb)
+        if ns >= 3:
+            q[2] += CX[i] * rb
+    return q
+
+
+@pytest.mark.parametrize("ns", [2, 3])
+def test_outflux_is_first_moment_of_post_collision_state(ns):
+    """Sec. III.A.3: N_s = (1/ny) sum_y sum_i c_ix g*_{s,i}(x_p, y) over the
+    post-collision populations.  The x-moment of the BGK update is
+    (1 - w) j_s + w C_s u_x (the equilibrium's first moment is C u), plus
+    the x-moment of the source on catalytic links, so on any state
+    N_s = (1/ny) sum_y [(1 - w_s) j_s + w_s C_s u_x + sum_i c_ix Q_{s,i}].
+    Random non-equilibrium states, planes cut by catalytic fibers of both
+    kinds.  A pre-collision reading, a plane one node off, the opposite
+    sign or a dropped source each miss by far more than the tolerance."""
+    nx, ny = 26, 11
+    fib = [[9.3, 4.6, 2.2, 1, 0, -1], [15.8, 6.1, 2.4, 2, 0, -1],
+           [12.4, 9.7, 1.5, 3, 0.4, -1]]
+    solid, kab, kbc = oracle.raster(nx, ny, fib, 0.3, 0.45)
+    rng = np.random.default_rng(11 + ns)
+    ux = (0.03 + 0.04 * rng.random((ny, nx))) * (solid == 0)
+    uy = 0.03 * (rng.random((ny, nx)) - 0.5) * (solid == 0)
+    tau = [0.9, 0.66, 1.4][:ns]
+    prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, tau, [1, 0, 0][:ns])
+    g = rng.random((ns, ny, nx, 9)) * (solid == 0)[None, :, :, None]
+    checked_source = 0
+    for xp in (7, 11, 12, 14, nx - 3):
+        want = np.zeros(ns)
+        pre = np.zeros(ns)
+        nosrc = np.zeros(ns)
+        for y in range(ny):
+            if solid[y, xp]:
+                continue
+            gi = g[:, y, xp, :]
+            c = gi.sum(axis=1)
+            j = (gi * CX).sum(axis=1)
+            om = 1.0 / np.asarray(tau)
+            q = _source_x_moment(ns, kab, kbc, solid, c, xp, y)
+            want += (1 - om) * j + om * c * ux[y, xp] + q
+            nosrc += (1 - om) * j + om * c * ux[y, xp]
+            pre += j
+        want /= ny
+        got = prob.flux(g, xp)[:ns]
+        scale = np.abs(want).max()
+        assert np.allclose(got, want, rtol=0, atol=1e-14 * max(scale, 1))
+        # the plausible misreadings are far away
+        assert np.abs(pre / ny - got).max() > 1e-3 * scale
+        assert np.abs(-want - got).max() > 1e-3 * scale
+        other = prob.flux(g, xp + 1)[:ns]
+        assert np.abs(other - got).max() > 1e-3 * scale
+        if np.abs(nosrc / ny - want).max() > 1e-3 * scale:
+            checked_source += 1
+    assert checked_source >= 2
+
+
+def test_outflux_of_equilibrium_state_in_poiseuille_flow():
+    """At an equilibrium state g = g^eq(C, u) with no catalyst, collision
+    changes nothing and the first moment of g^eq is C u_x, so
+    N_s = (1/ny) sum_y C_s(y) u_x(x_p, y) exactly.  With C = 1 on the steady
+    empty channel this is the plane-mean of u_x: the parabola's mean
+    (2/3) u0 (1 + 1/(2 ny^2)) divided by the density on the plane."""
+    nx, ny, u0 = 48, 14, 0.05
+    solid = np.zeros((ny, nx), np.uint8)
+    rho, ux, uy, res = oracle.flow_run(solid, 0.8, u0, 6000)
+    assert res < 1e-8
+    z = np.zeros((ny, nx))
+    prob = oracle.ADRProblem(solid, z, z, ux, uy, [0.7, 0.8, 1.1], [1, 0, 0])
+    yy = np.arange(ny, dtype=float)
+    c0 = np.stack([np.ones((ny, nx)),
+                   np.broadcast_to((0.2 + 0.05 * yy)[:, None], (ny, nx)),
+                   np.broadcast_to(np.cos(0.3 * yy)[:, None] ** 2, (ny, nx))])
+    g = prob.init(c0)
+    xp = nx - 3
+    got = prob.flux(g, xp)
+    want = (c0[:, :, xp] * ux[None, :, xp]).sum(axis=1) / ny
+    assert np.allclose(got, want, rtol=1e-13, atol=0)
+    # the flow carries the parabola's mass flux, rho u_x, through every
+    # column; rho varies along x with the pressure drop but barely across
+    # the plane, so the plane-mean of u_x is the parabola's mean over rho
+    mean_para = (2.0 / 3.0) * u0 * (1 + 1 / (2 * ny * ny))
+    rp = rho[:, xp]
+    assert rp.max() - rp.min() < 2e-3
+    assert got[0] == pytest.approx(mean_para / rp.mean(), rel=1e-3)
+
+
+def _face_fluxes(g, solid, cin):
+    """Net flux of the species sum through every face x = -1/2 .. nx - 1/2
+    of the pre-collision steady state g (the step maps it to itself), per
+    Eq. (BC): the inlet face from the anti-bounce-back of species A
+    (g_i(0) = -g*_opp + 2 w_i c_in, so the face carries
+    sum_y [2 sum_{c_ix>0} g_i(0, y) - c_in/3]; B and C bounce back and carry
+    nothing); the outlet face from g_opp(nx-1) = -g*_i + 2 w_i C_b, i.e.
+    sum_y [C_b/3 - 2 sum_{c_ix<0} g_i(nx-1, y)]; an interior face from the
+    populations that streamed across it (bounced ones stay)."""
+    ns, ny, nx, _ = g.shape
+    fl = solid == 0
+    out = np.zeros(nx + 1)
+    for s in range(ns):
+        if cin[s] != 0 or s == 0:
+            out[0] += (2 * g[s][:, 0, PLUS].sum(axis=1) - cin[s] / 3)[fl[:, 0]].sum()
+        for x in range(nx - 1):
+            f = 0.0
+            for y in range(ny):
+                for i in PLUS:      # arrived at (x+1, y) from (x, y - c_iy)
+                    sy = y - CY[i]
+                    if fl[y, x + 1] and 0 <= sy < ny and fl[sy, x]:
+                        f += g[s, y, x + 1, i]
+                for i in MINUS:     # arrived at (x, y) from (x+1, y - c_iy)
+                    sy = y - CY[i]
+                    if fl[y, x] and 0 <= sy < ny and fl[sy, x + 1]:
+                        f -= g[s, y, x, i]
+            out[x + 1] += f
+        cb = g[s][:, nx - 1, :].sum(axis=1)
+        out[nx] += (cb / 3 - 2 * g[s][:, nx - 1, MINUS].sum(axis=1))[
+            fl[:, nx - 1]].sum()
+    return out
+
+
+def _landed_flux(g, solid, xp):
+    """ny N_s rebuilt from the streaming map: at a steady state each
+    post-collision population g*_i(x_p, y) is found in the next pre-collision
+    state at its neighbour (x_p + c_i) when that is a fluid node, else bounced
+    back in place as g_opp(x_p, y)."""
+    ns, ny, nx, _ = g.shape
+    fl = solid == 0
+    out = np.zeros(ns)
+    for y in range(ny):
+        if not fl[y, xp]:
+            continue
+        for i in PLUS + MINUS:
+            tx, ty = xp + CX[i], y + CY[i]
+            if 0 <= ty < ny and fl[ty, tx]:
+                out += CX[i] * g[:, ty, tx, i]
+            else:
+                out += CX[i] * g[:, y, xp, OPP[i]]
+    return out
+
+
+@pytest.mark.parametrize("k", [1.0, 0.0])
+def test_steady_flux_conservation_and_outflux(k):
+    """p6 (Sec. III.A.3; the sources of Eq. source_lbm add to zero, collision
+    and bounce-back keep mass): at the steady state of a cascade channel
+    (per-step residual < 1e-13) the A injected through the inlet leaves as
+    A + B + C, and the same net flux crosses every face.  The outflux N_s on
+    a plane is the post-collision first moment, which the streaming map
+    returns exactly.  The paper's node-centred N at x_p = nx - 3 differs
+    from the conserved face flux by a lattice-spacing effect near the outlet
+    (0.6-0.8% on this 60 x 16 lattice); it must stay within 1%.  With k = 0
+    no B or C exists anywhere."""
+    nx, ny = 60, 16
+    fib = [[20.2, 8.3, 3.0, 1, 0, -1], [35.5, 7.1, 3.0, 2, 0, -1],
+           [27.6, 1.2, 2.0, 3, 0.5, -1]]
+    solid, kab, kbc = oracle.raster(nx, ny, fib, 0.05, 0.08)
+    _, ux, uy, fres = oracle.flow_run(solid, 0.8, 0.05, 6000)
+    assert fres < 1e-8
+    cin = [1.0, 0.0, 0.0]
+    prob = oracle.ADRProblem(solid, kab * k, kbc * k, ux, uy,
+                             [0.62, 0.7, 0.8], cin)
+    out = prob.solve(1e-13, 500, 200000)
+    assert out["converged"]
+    g = out["g"]
+    faces = _face_fluxes(g, solid, cin)
+    f_in = faces[0]
+    assert f_in > 0.3
+    assert np.abs(faces - f_in).max() < 1e-9 * f_in
+    for xp in (nx - 3, 21, 28, 36, 45):
+        n = prob.flux(g, xp)
+        assert np.allclose(n * ny, _landed_flux(g, solid, xp), rtol=0,
+                           atol=1e-11 * f_in)
+    n = out["flux"]
+    assert abs(n.sum() * ny - f_in) < 1e-2 * f_in
+    if k == 0.0:
+        assert n[1] == 0.0 and n[2] == 0.0
+    else:
+        assert n[1] > 1e-3 and n[2] > 1e-3
 
 
 def test_no_reaction_no_product():
