@@ -51,7 +51,8 @@ def _args():
     ap.add_argument("--fibers-per-band", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="large",
-                    choices=["large", "sweep", "adjoint", "series"],
+                    choices=["large", "sweep", "adjoint", "series",
+                             "cascade"],
                     help="large: the 67M-node membrane (default line); "
                          "sweep: the 64-instance Pe x Da sweep, batched "
                          "FP32 / FP16 against unbatched FP64 (solves/s); "
@@ -59,7 +60,10 @@ def _args():
                          "67M-node membrane (f32 or f64); series: the "
                          "paper's 2D experiment series (isolated fiber, "
                          "fiber pairs, side-by-side fiber against Pe), "
-                         "batched, to steady state")
+                         "batched, to steady state; cascade: the "
+                         "two-membrane cascade (2048x512) at Da = 1 and "
+                         "Pe = 1, 10, 100 to steady state in FP64 and "
+                         "FP32")
     ap.add_argument("--adjoint-iters", type=int, default=200)
     ap.add_argument("--sweep-instances", type=int, default=64)
     ap.add_argument("--sweep-max-steps", type=int, default=5000)
@@ -68,6 +72,8 @@ def _args():
                          "runs every instance exactly --sweep-max-steps "
                          "steps in every precision")
     ap.add_argument("--sweep-flow-steps", type=int, default=3000)
+    ap.add_argument("--cascade-pe", default="1,10,100")
+    ap.add_argument("--cascade-max-steps", type=int, default=3000000)
     return ap.parse_args()
 
 
@@ -164,12 +170,10 @@ def _peak_hbm():
 
 
 KERNEL_SOURCES = {
-    "f32": ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "lbm_tma.cuh",
-            "kernels_f32.cu"),
-    "f16dev": ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "lbm_tma.cuh",
-               "lbm_f16.cuh", "kernels_f16dev.cu"),
-    "f64": ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "lbm_tma.cuh",
-            "kernels_f64.cu"),
+    "f32": ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "kernels_f32.cu"),
+    "f16dev": ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "lbm_f16.cuh",
+               "kernels_f16dev.cu"),
+    "f64": ("lbm_kernels.cuh", "lbm_launch_impl.cuh", "kernels_f64.cu"),
 }
 
 
@@ -713,6 +717,86 @@ def run_series(a):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the two-membrane cascade to steady state
+# ---------------------------------------------------------------------------
+def run_cascade(a):
+    """Two-membrane cascade lattice (2048 x 512, 40 + 40 R = 8 fibers,
+    seed 0), Da1 = Da2 = 1, per Pe: FP64 ADR to a per-step residual of 1e-9
+    and FP32 to 1e-6 (checked every 1000 steps); then FP32 and
+    FP16-deviation storage run exactly FP64's step count, so that their
+    efficiencies are compared with FP64's at equal steps.  Untimed: the
+    FP64 flow to a per-step residual of 1e-9 (shared by every Pe, since u0
+    is fixed and Pe only sets D).  Timed with CUDA events: each solve.
+    Reports per Pe and precision the steps, seconds, the outlet efficiency
+    of Eq. (A-B) on x = nx - 3, its difference to FP64, the outflux shares
+    and the most negative concentration met at the last check."""
+    import torch
+
+    from paper_2109_04455_gb300 import inputs, lbm
+    torch.cuda.set_device(0)
+    pes = [float(v) for v in a.cascade_pe.split(",")]
+    w0 = inputs.two_membrane_cascade(seed=0, pe=pes[0])
+    geom = lbm.Geometry(w0.nx, w0.ny, w0.fibers, w0.k1, w0.k2)
+    geom.upload()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+        enable_timing=True)
+    ev0.record()
+    u64, finfo = lbm.lbm_flow_solve(geom, w0.tau_flow, w0.u0, 1000000,
+                                    tol=1e-9, check_every=1000,
+                                    precision=lbm.LBM_F64)
+    ev1.record()
+    torch.cuda.synchronize()
+    out = {"metric": "two-membrane cascade steady solves (ADR, 3 species)",
+           "unit": "s", "lattice": f"{w0.nx}x{w0.ny}",
+           "fibers": int(w0.fibers.shape[0]),
+           "flow": {"steps": finfo["steps"], "residual": finfo["residual"],
+                    "converged": finfo["converged"],
+                    "seconds": ev0.elapsed_time(ev1) * 1e-3},
+           "runs": []}
+    u32 = u64.float()
+
+    def solve(w, prec, tol, steps):
+        g = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
+        prm = lbm.adr_params(3, w.tau_c, precision=prec, max_steps=steps,
+                             tol=tol, check_every=1000)
+        torch.cuda.synchronize()
+        ev0.record()
+        try:
+            _, info = lbm.lbm_adr_solve(g, prm, u64 if prec == lbm.LBM_F64
+                                        else u32, want_conc=False)
+            status = "ok" if info["converged"] or tol <= 0 else "not converged"
+        except lbm.LBMError as e:
+            info, status = {"steps": None, "eps": None, "flux": [None] * 3,
+                            "residual": None, "c_min": [None] * 3}, str(e)
+        ev1.record()
+        torch.cuda.synchronize()
+        fl = info["flux"]
+        tot = sum(fl) if None not in fl else None
+        return {"steps": info["steps"], "residual": info["residual"],
+                "eps": info["eps"], "status": status,
+                "flux_share": [f / tot for f in fl] if tot else None,
+                "c_min": info["c_min"],
+                "seconds": ev0.elapsed_time(ev1) * 1e-3}
+
+    for pe in pes:
+        w = inputs.two_membrane_cascade(seed=0, pe=pe)
+        row = {"pe": pe, "tau_c": w.tau_c, "k1": w.k1, "k2": w.k2}
+        r64 = solve(w, lbm.LBM_F64, 1e-9, a.cascade_max_steps)
+        row["f64_to_1e-9"] = r64
+        row["f32_to_1e-6"] = solve(w, lbm.LBM_F32, 1e-6, a.cascade_max_steps)
+        if r64["steps"]:
+            for name, prec in (("f32_equal_steps", lbm.LBM_F32),
+                               ("f16dev_equal_steps", lbm.LBM_F16DEV)):
+                row[name] = solve(w, prec, 0.0, r64["steps"])
+            for k in ("f32_to_1e-6", "f32_equal_steps", "f16dev_equal_steps"):
+                if row[k]["eps"] is not None and r64["eps"] is not None:
+                    row[k]["eps_err_vs_f64"] = abs(row[k]["eps"] - r64["eps"])
+        out["runs"].append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -723,6 +807,8 @@ def main():
         run_adjoint(a)
     elif a.workload == "series":
         run_series(a)
+    elif a.workload == "cascade":
+        run_cascade(a)
     else:
         run_gpu(a)
 

@@ -44,7 +44,8 @@ typedef enum {
   LBM_ENOMEM = 2,         /* a caller-provided workspace is too small      */
   LBM_ECUDA = 3,          /* a CUDA runtime call or kernel launch failed   */
   LBM_ENOTCONVERGED = 4,  /* max_steps reached above the tolerance          */
-  LBM_EUNSTABLE = 5       /* NaN or Inf met in the residual / flux sums     */
+  LBM_EUNSTABLE = 5       /* NaN or Inf met in the residual / flux sums, or
+                             (ADR) a concentration below -neg_tol           */
 } lbm_status;
 
 typedef enum {
@@ -109,6 +110,20 @@ lbm_status lbm_geometry_fields(const lbm_geometry *g, uint8_t *solid,
 lbm_status lbm_geometry_set_rates(lbm_geometry *g, const double *kab,
                                   const double *kbc);
 
+/* Periodic edges (Sec. IV.B: the pure-diffusion cascade runs in a box that
+ * is periodic in every direction, without flow).  LBM_PERIODIC_X joins the
+ * x edges (no inlet and no outlet: a population leaving at x = nx - 1/2
+ * enters at x = -1/2 and the reverse), LBM_PERIODIC_Y the y edges (no
+ * walls).  A fiber node across an edge bounces back and reacts with its own
+ * rates, as anywhere else.  Rebuilds the link words; as after
+ * lbm_geometry_set_rates, upload again before creating solvers.  Flags 0
+ * restores the channel (inlet, outlet, walls).  The flow lattice's inlet
+ * and outlet rules then apply to no link: a periodic box has no imposed
+ * flow, and an ADR solve in it is usually given u = 0. */
+#define LBM_PERIODIC_X 1
+#define LBM_PERIODIC_Y 2
+lbm_status lbm_geometry_set_periodic(lbm_geometry *g, int32_t flags);
+
 /* Device bytes lbm_geometry_upload needs. */
 size_t lbm_geometry_ws_bytes(const lbm_geometry *g);
 
@@ -125,6 +140,15 @@ typedef struct {
   int32_t converged; /* 1 if residual < tol at the last check              */
   double flux[3];    /* outfluxes N_A, N_B, N_C (ADR only)                  */
   double eps;        /* efficiency (ADR only; 0 if undefined)               */
+  double c_min[3];   /* ADR: most negative concentration of each species at
+                        the last (checked) step, 0 if none is negative.
+                        The explicit scheme is not positivity preserving:
+                        near tau -> 1/2 (high Pe) sharp fronts undershoot,
+                        and a diverging lattice shows up here long before
+                        its sums overflow                                   */
+  double mass[3];    /* ADR: sum over the lattice of |C_s| at the last step
+                        (the amount of each species when C_s >= 0; the
+                        residual's denominator)                             */
 } lbm_solve_info;
 
 /* ------------------------------------------------------------------------ */
@@ -187,6 +211,10 @@ typedef struct {
   int32_t check_every; /* lbm_adr_solve: steps per check (>= 2)             */
   int32_t x_plane;     /* flux plane; < 0 selects nx - 3                    */
   int32_t flags;       /* LBM_ADR_* bits                                    */
+  double neg_tol;      /* checked steps report LBM_EUNSTABLE when some C_s
+                          < -neg_tol * max(1, c_in[0..nspecies)); 0 selects
+                          0.1, < 0 turns the test off (c_min is reported
+                          either way)                                        */
 } lbm_adr_params;
 
 /* Device bytes of the ADR workspace (two population buffers, the
@@ -207,9 +235,12 @@ void lbm_adr_destroy(lbm_adr_solver *s);
 lbm_status lbm_adr_init(lbm_adr_solver *s, void *stream);
 
 /* Advance nsteps time steps.  info == NULL: enqueue only (no host sync).
- * info != NULL (nsteps >= 2): the last two steps also record C and the
- * residual, the outflux on the plane is reduced, the stream is synchronised
- * and info is filled; LBM_EUNSTABLE if a sum is not finite. */
+ * info != NULL (nsteps >= 2): the last two steps also record C, the
+ * residual (its per-node terms summed in double), the amount of each
+ * species and the most negative concentration at the last step, the
+ * outflux on the plane is reduced, the stream is synchronised and info is
+ * filled; LBM_EUNSTABLE (info still filled) if a sum is not finite or a
+ * concentration is below -neg_tol (see lbm_adr_params). */
 lbm_status lbm_adr_run(lbm_adr_solver *s, int64_t nsteps, void *stream,
                        lbm_solve_info *info);
 
@@ -315,9 +346,104 @@ lbm_status lbm_batch_tuning(const lbm_batch *b, int32_t *tile, int32_t *grid,
                             float *ms_per_step);
 
 /* Solve every lattice from its initial state; infos[count] receives steps,
- * residual, converged, outfluxes and efficiency per lattice.
+ * residual, converged, outfluxes, efficiency and c_min per lattice.  A
+ * lattice whose sums go non-finite or whose concentration falls below
+ * -neg_tol stops there (LBM_EUNSTABLE overall, the others run on).
  * LBM_ENOTCONVERGED if any lattice stopped at max_steps. */
 lbm_status lbm_batch_solve(lbm_batch *b, void *stream, lbm_solve_info *infos);
+
+/* Concentrations of lattice `index` at its last checked step (after
+ * lbm_batch_solve: its final state), copied to conc_out (device,
+ * [nspecies][ny][nx_pad] of that lattice, double for LBM_F64 else float)
+ * on `stream`.  LBM_EINVAL for a bad index or before any solve. */
+lbm_status lbm_batch_conc(const lbm_batch *b, int32_t index, void *conc_out,
+                          void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Random walk particle tracking (Sec. III.B), the paper's second method for */
+/* the efficiency of a 2D cross-section.  Per time step dt (the paper: 0.5)  */
+/* a particle moves by dt u(x) (u bilinear in the LBM velocity field, nodes  */
+/* at integer positions, indices clamped to the lattice) and by a step of    */
+/* length sqrt(4 D dt) in a uniformly random direction; it reflects          */
+/* elastically off the walls y = -1/2, ny - 1/2 and off every fiber (a disc  */
+/* of radius R + radius_offset: 0.5 puts the surface where the LBM's halfway */
+/* bounce-back puts it); within the reactive shell of width delta (the       */
+/* paper: 0.2) around a catalytic fiber it reacts with probability k dt      */
+/* (A -> B at the fiber's k_AB, B -> C at its k_BC; side-by-side fibers by    */
+/* side, relaxed weights as in lbm_geometry_create; the first fiber in list  */
+/* order whose shell holds the particle decides; one reaction per step).     */
+/* The entrance strip x in [-1/2, 1/2) is held at `density` particles of A   */
+/* per unit area: each step the A particles that end there are removed and  */
+/* the strip seeded anew; A crossing x = -1/2 returns to that reservoir, B   */
+/* and C reflect there.  A particle crossing x = nx - 1/2 leaves and counts  */
+/* for its species; eps follows Eq. (A-B) from these counts.  Random numbers */
+/* come from per-particle SplitMix64 streams (draw k of particle `id` at     */
+/* step t: output 64 t + k + 1 of the stream seeded by output id + 1 of the  */
+/* stream of `seed`), and every arithmetic step is one IEEE operation, so a  */
+/* run is reproducible bit for bit whatever the storage order.               */
+/* ------------------------------------------------------------------------ */
+#define LBM_RWPT_PERIODIC 1    /* box periodic in x and y: no inlet, outlet,
+                                  walls or entrance strip (positions wrap)   */
+#define LBM_RWPT_HOMOGENEOUS 2 /* every particle reacts with k1 dt (A) and
+                                  k2 dt (B) per step wherever it is (the
+                                  homogeneous-reaction check of Appendix C)  */
+typedef struct {
+  double D;              /* diffusivity                                      */
+  double dt;             /* time step                                        */
+  double delta;          /* reactive shell width                             */
+  double density;        /* particles per unit area: entrance strip and the
+                            initial fill of the box with A                   */
+  double radius_offset;  /* reflecting radius = R + radius_offset            */
+  uint64_t seed;
+  int32_t nspecies;      /* 1, 2 or 3                                        */
+  int32_t flags;         /* LBM_RWPT_* bits                                  */
+} lbm_rwpt_params;
+
+typedef struct {
+  int64_t steps;         /* steps since lbm_rwpt_init                        */
+  int64_t window_steps;  /* steps since the counts were last reset           */
+  int64_t alive;         /* particles in the box                             */
+  int64_t out[3];        /* particles of A, B, C that left through the outlet
+                            in the window                                    */
+  double eps;            /* Eq. (A-B) from out[] (0 if undefined)            */
+  int32_t overflow;      /* 1 if the capacity was exceeded (LBM_ENOMEM)      */
+} lbm_rwpt_info;
+
+typedef struct lbm_rwpt lbm_rwpt;
+
+/* Device bytes for `capacity` particles and `nfibers` fibers. */
+size_t lbm_rwpt_ws_bytes(int64_t capacity, int32_t nfibers);
+
+/* Bind a particle system to a channel of nx x ny nodes, a fiber table (host,
+ * rows of 6 doubles as in lbm_geometry_create, with rates k1 and k2 per
+ * unit time), the device velocity u ([2][ny][nx_pad] double, or NULL for no
+ * flow) and the workspace ws.  LBM_EINVAL for k dt > 1. */
+lbm_status lbm_rwpt_create(int32_t nx, int32_t ny, const double *fibers,
+                           int32_t nfibers, double k1, double k2,
+                           const lbm_rwpt_params *p, const void *u,
+                           int64_t capacity, void *ws, size_t ws_bytes,
+                           lbm_rwpt **out);
+void lbm_rwpt_destroy(lbm_rwpt *r);
+
+/* Fill the box with A at the density (none inside the fibers), step 0,
+ * counts 0. */
+lbm_status lbm_rwpt_init(lbm_rwpt *r, void *stream);
+
+/* Advance nsteps steps (no host synchronisation when info is NULL);
+ * with info, synchronise and report.  LBM_ENOMEM if the capacity was ever
+ * exceeded (the surplus particles were dropped). */
+lbm_status lbm_rwpt_run(lbm_rwpt *r, int64_t nsteps, void *stream,
+                        lbm_rwpt_info *info);
+
+/* Zero the outlet counts and start a new window. */
+lbm_status lbm_rwpt_reset_counts(lbm_rwpt *r, void *stream);
+
+/* Copy the particles (in storage order, which varies from run to run) to
+ * host arrays of max_count entries; *count receives their number
+ * (LBM_ENOMEM if it exceeds max_count). */
+lbm_status lbm_rwpt_particles(lbm_rwpt *r, void *stream, int64_t max_count,
+                              int64_t *count, double *x, double *y,
+                              int32_t *species, uint64_t *id);
 
 /* Eq. (A-B): eps = N_B/(N_A+N_B) for nspecies 2, N_C/(N_A+N_B+N_C) for 3.
  * Host arithmetic only.  LBM_EINVAL for other nspecies or a zero sum. */
@@ -333,12 +459,14 @@ lbm_status lbm_efficiency(const double *flux, int32_t nspecies, double *eps);
  * implicit device synchronisation.  Its partial sums live in a fixed 6 KB
  * device array that every GPU loading this library holds until the process
  * exits; it covers at most 65536 lattice rows, and a larger ny is rejected
- * with LBM_EINVAL.  The first call on a device looks up that array's device
- * address, so make the first call before any stream capture.  All calls
- * share the one array and it keeps the last call's values (each call
- * rewrites every slot it reads, so nothing needs clearing); calls whose GPU
- * work overlaps (other streams or threads) race on it and must be
- * serialised by the caller.  Synchronises `stream`. */
+ * with LBM_EINVAL.  Every call looks up that array's device address on the
+ * solver's device (cudaGetSymbolAddress, which allocates nothing), so the
+ * address stays right after a device reset; the call synchronises `stream`,
+ * so it is not for use inside a stream capture.  All calls share the one
+ * array and it keeps the last call's values (each call rewrites every slot
+ * it reads, so nothing needs clearing); calls whose GPU work overlaps
+ * (other streams or threads) race on it and must be serialised by the
+ * caller. */
 lbm_status lbm_adr_outflux_noalloc(lbm_adr_solver *s, int32_t x_plane,
                                    void *stream, double *flux_out);
 

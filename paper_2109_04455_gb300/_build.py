@@ -14,10 +14,10 @@ LIB = os.path.join(HERE, "liblbm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 CU_SOURCES = ["lbm_api.cu", "kernels_f64.cu", "kernels_f32.cu",
-              "kernels_f16dev.cu", "lbm_batch.cu"]
+              "kernels_f16dev.cu", "lbm_batch.cu", "lbm_rwpt.cu"]
 CPP_SOURCES = ["geometry.cpp"]
 HEADERS = ["lbm_internal.h", "lbm_kernels.cuh", "lbm_launch_impl.cuh",
-           "lbm_tma.cuh", "lbm_f16.cuh", "lbm_nvtx.h", "lbm_adjoint.cuh"]
+           "lbm_f16.cuh", "lbm_nvtx.h", "lbm_adjoint.cuh"]
 
 
 def _cu_cmd(src, obj):

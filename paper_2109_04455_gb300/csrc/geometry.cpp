@@ -17,9 +17,14 @@ namespace {
 
 // Link words of the fluid nodes (nibble j-1: type of the neighbour x + c_j,
 // a solid neighbour being catalytic when either of its rates is non-zero),
-// the boundary-node list and the solid count.
+// the boundary-node list and the solid count.  Across a periodic edge the
+// neighbour is the wrapped node (kPeriodic when it is fluid); otherwise the
+// x edges are the inlet and the outlet (their rule wins on corner links) and
+// the y edges walls.
 void build_links(lbm_geometry *g) {
   const int64_t nx = g->nx, ny = g->ny;
+  const bool px = (g->periodic & LBM_PERIODIC_X) != 0;
+  const bool py = (g->periodic & LBM_PERIODIC_Y) != 0;
   g->links.assign(static_cast<size_t>(g->nx_pad) * ny, kSolidNode);
   g->bnodes.clear();
   int64_t nsol = 0;
@@ -32,19 +37,31 @@ void build_links(lbm_geometry *g) {
       }
       uint32_t word = 0;
       for (int j = 1; j < 9; ++j) {
-        const int64_t tx = x + kCx[j], ty = y + kCy[j];
-        uint32_t t;
-        if (tx < 0)
-          t = kInlet;  // the x-boundary rule wins on corner links
-        else if (tx >= nx)
-          t = kOutlet;
-        else if (ty < 0 || ty >= ny)
-          t = kWall;
-        else if (g->solid[ty * nx + tx]) {
-          const int64_t m = ty * g->nx_pad + tx;
-          t = (g->kab[m] != 0.0 || g->kbc[m] != 0.0) ? kCat : kInert;
-        } else
-          t = kFluid;
+        int64_t tx = x + kCx[j], ty = y + kCy[j];
+        bool wrapped = false;
+        uint32_t t = kFluid;
+        if ((tx < 0 || tx >= nx) && !px) {
+          t = tx < 0 ? kInlet : kOutlet;
+        } else {
+          if (tx < 0 || tx >= nx) {
+            tx = (tx + nx) % nx;
+            wrapped = true;
+          }
+          if ((ty < 0 || ty >= ny) && !py) {
+            t = kWall;
+          } else {
+            if (ty < 0 || ty >= ny) {
+              ty = (ty + ny) % ny;
+              wrapped = true;
+            }
+            if (g->solid[ty * nx + tx]) {
+              const int64_t m = ty * g->nx_pad + tx;
+              t = (g->kab[m] != 0.0 || g->kbc[m] != 0.0) ? kCat : kInert;
+            } else {
+              t = wrapped ? kPeriodic : kFluid;
+            }
+          }
+        }
         word |= t << (4 * (j - 1));
       }
       g->links[n] = word;
@@ -212,6 +229,23 @@ extern "C" lbm_status lbm_geometry_set_rates(lbm_geometry *g,
     build_links(g);
   } catch (const std::bad_alloc &) {
     set_error("lbm_geometry_set_rates: host allocation failed");
+    return LBM_ENOMEM;
+  }
+  g->uploaded = false;   // the device copy is stale until the next upload
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_geometry_set_periodic(lbm_geometry *g,
+                                                int32_t flags) {
+  if (!g || (flags & ~(LBM_PERIODIC_X | LBM_PERIODIC_Y))) {
+    set_error("lbm_geometry_set_periodic: NULL geometry or unknown flags");
+    return LBM_EINVAL;
+  }
+  try {
+    g->periodic = flags;
+    build_links(g);
+  } catch (const std::bad_alloc &) {
+    set_error("lbm_geometry_set_periodic: host allocation failed");
     return LBM_ENOMEM;
   }
   g->uploaded = false;   // the device copy is stale until the next upload

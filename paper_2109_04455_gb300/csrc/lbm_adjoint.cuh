@@ -38,10 +38,10 @@ struct AdjArgs {
 
 enum AdjMode { kAdjStep = 0, kAdjCheck = 1 };
 
-// mu = P^T nu + l of species s at fluid node n (link word lw)
+// mu = P^T nu + l of species s at fluid node n = y nx_pad + x (link word lw)
 template <typename T>
 __device__ __forceinline__ void adj_gather(const AdjArgs &a, int s, uint32_t lw,
-                                           long long n, int x, T (&mu)[9]) {
+                                           long long n, int x, int y, T (&mu)[9]) {
   const T *nu = static_cast<const T *>(a.src) + (long long)s * 9 * a.plane;
   const long long np = a.nx_pad, plane = a.plane;
   mu[0] = nu[n];
@@ -51,6 +51,8 @@ __device__ __forceinline__ void adj_gather(const AdjArgs &a, int s, uint32_t lw,
     const uint32_t t = lw == 0u ? (uint32_t)kFluid : nib(lw, i);
     if (t == kFluid) {
       mu[i] = nu[(long long)i * plane + n + cy(i) * np + cx(i)];
+    } else if (t == kPeriodic) {
+      mu[i] = nu[(long long)i * plane + neighbour(x, y, i, a.nx, a.ny, np)];
     } else {
       const T back = nu[(long long)opp(i) * plane + n];
       if (t == kInlet) {
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kBlockX) adj_kernel(const AdjArgs a) {
     adj_eq<T>(a, n, E);
     T mu[NS][9];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) adj_gather<T>(a, s, lw, n, x, mu[s]);
+    for (int s = 0; s < NS; ++s) adj_gather<T>(a, s, lw, n, x, y, mu[s]);
     T R[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) R[s] = T(0);
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(kBlockX) adj_kernel(const AdjArgs a) {
 #pragma unroll
     for (int j = 1; j < 9; ++j) {
       if (nib(lw, j) != kCat) continue;
-      const long long m = n + cy(j) * np + cx(j);
+      const long long m = neighbour(x, y, j, a.nx, a.ny, np);
       const T wj = Lattice<T>::w(j);
       const T ka = T(a.kab[m]) * wj;
       R[0] += ka * ((NS >= 2 ? mu[NS >= 2 ? 1 : 0][j] : T(0)) - mu[0][j]);
@@ -196,9 +198,10 @@ __global__ void __launch_bounds__(kBlockX)
   const long long n = bnodes[t];
   const uint32_t lw = a.links[n];
   const int x = static_cast<int>(n % a.nx_pad);
+  const int y = static_cast<int>(n / a.nx_pad);
   T mu[NS][9];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) adj_gather<T>(a, s, lw, n, x, mu[s]);
+  for (int s = 0; s < NS; ++s) adj_gather<T>(a, s, lw, n, x, y, mu[s]);
   const T cA = conc[n];
   const T cB = NS >= 2 ? conc[a.plane + n] : T(0);
   const long long np = a.nx_pad;
@@ -206,7 +209,7 @@ __global__ void __launch_bounds__(kBlockX)
   for (int j = 1; j < 9; ++j) {
     const uint32_t ty = nib(lw, j);
     if (ty != kCat && ty != kInert) continue;
-    const long long m = n + cy(j) * np + cx(j);
+    const long long m = neighbour(x, y, j, a.nx, a.ny, np);
     const double wj = double(Lattice<T>::w(j));
     double ga = -double(mu[0][j]);
     if (NS >= 2) ga += double(mu[NS >= 2 ? 1 : 0][j]);

@@ -3,7 +3,6 @@
 // is the caller's; this file only launches kernels on the caller's stream.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <string>
 
@@ -16,27 +15,26 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
-template <int K>
+template <int KS, int KM>
 static cudaError_t reduce_two_level(const double *partials, long long nb,
                                    double *scratch, double *out,
                                    cudaStream_t st) {
   const dim3 block(kReduceThreads);
   const long long g = nb < kReduceGrid ? (nb > 0 ? nb : 1) : kReduceGrid;
   const long long chunk = (nb + g - 1) / g;
-  reduce_partials_kernel<K><<<static_cast<unsigned>(g), block, 0, st>>>(
+  reduce_partials_kernel<KS, KM><<<static_cast<unsigned>(g), block, 0, st>>>(
       partials, nb, chunk, scratch);
-  reduce_partials_kernel<K><<<1, block, 0, st>>>(scratch, g, g, out);
+  reduce_partials_kernel<KS, KM><<<1, block, 0, st>>>(scratch, g, g, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce(int k, const double *partials, long long nb,
+cudaError_t launch_reduce(int ks, int km, const double *partials, long long nb,
                           double *scratch, double *out, cudaStream_t st) {
-  switch (k) {
-    case 2: return reduce_two_level<2>(partials, nb, scratch, out, st);
-    case 4: return reduce_two_level<4>(partials, nb, scratch, out, st);
-    case 6: return reduce_two_level<6>(partials, nb, scratch, out, st);
-    default: return cudaErrorInvalidValue;
-  }
+  if (ks == 2 && km == 0) return reduce_two_level<2, 0>(partials, nb, scratch, out, st);
+  if (ks == 2 && km == 1) return reduce_two_level<2, 1>(partials, nb, scratch, out, st);
+  if (ks == 4 && km == 2) return reduce_two_level<4, 2>(partials, nb, scratch, out, st);
+  if (ks == 6 && km == 3) return reduce_two_level<6, 3>(partials, nb, scratch, out, st);
+  return cudaErrorInvalidValue;
 }
 
 namespace {
@@ -252,7 +250,7 @@ extern "C" lbm_status lbm_flow_solve(const lbm_geometry *g,
     cudaError_t e2 = step(kFlowU);
     if (e2 == cudaSuccess) e2 = step(kFlowCheck);
     if (e2 == cudaSuccess)
-      e2 = launch_reduce(2, partials, grid_blocks(g), scratch, result, st);
+      e2 = launch_reduce(2, 0, partials, grid_blocks(g), scratch, result, st);
     double h[2] = {0, 0};
     if (e2 == cudaSuccess)
       e2 = cudaMemcpyAsync(h, result, sizeof(h), cudaMemcpyDeviceToHost, st);
@@ -328,9 +326,9 @@ static AdrLayout adr_layout(const lbm_geometry *g, const lbm_adr_params *p) {
   l.partials = align256(static_cast<size_t>(adr_partial_rows(
                             g->nx_pad, g->ny,
                             static_cast<long long>(g->bnodes.size()))) *
-                        2 * ns * 8);
-  l.scratch = align256(kReduceGrid * 2 * ns * 8);
-  l.result = align256(64 * 8);
+                        3 * ns * 8);
+  l.scratch = align256(kReduceGrid * 3 * ns * 8);
+  l.result = align256(kResSlots * 8);
   // half storage: per-node reference concentrations of both buffers
   l.ref = p->precision == LBM_F16DEV ? align256(ns * pl * sizeof(RefT)) : 0;
   // FP64: the equilibrium factors E_i(u) of the frozen velocity [9][plane]
@@ -369,7 +367,7 @@ static cudaError_t adr_flux_launch(const lbm_adr_solver *s, cudaStream_t st) {
   int xp = s->p.x_plane < 0 ? g->nx - 3 : s->p.x_plane;
   const void *cur = s->buf[s->cur];
   const RefT *ref = s->rbuf[s->cur];
-  double *out = s->result + 8;
+  double *out = s->result + kResFlux;
   const int ns = s->p.nspecies;
   switch (s->p.precision) {
     case LBM_F64:
@@ -458,8 +456,6 @@ extern "C" lbm_status lbm_adr_create(const lbm_geometry *g,
   a.bnodes = g->d_bnodes;
   a.nbnd = static_cast<long long>(g->bnodes.size());
   a.part_off = 0;
-  // status word of the TMA-staged step (last double slot of the results)
-  a.status = reinterpret_cast<int *>(s->result + 15);
   a.plane = plane_of(g);
   a.nx = g->nx;
   a.ny = g->ny;
@@ -507,7 +503,7 @@ extern "C" lbm_status lbm_adr_init(lbm_adr_solver *s, void *stream) {
   cudaStream_t st = as_stream(stream);
   const AdrLayout l = adr_layout(s->g, &s->p);
   cudaError_t e = cudaMemsetAsync(s->buf[0], 0, 2 * l.buf + l.cprev, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->result, 0, 16 * sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->result, 0, kResSlots * sizeof(double), st);
   if (e == cudaSuccess && l.ref) e = cudaMemsetAsync(s->rbuf[0], 0, 2 * l.ref, st);
   if (e == cudaSuccess && s->a.etab)
     e = launch_eq_table(static_cast<const double *>(s->a.u), plane_of(s->g),
@@ -557,9 +553,9 @@ extern "C" lbm_status lbm_adr_run(lbm_adr_solver *s, int64_t nsteps,
   cudaError_t e = adr_step(s, kAdrCheck, st);
   if (e == cudaSuccess) e = adr_step(s, kAdrCheck, st);
   if (e == cudaSuccess)
-    e = launch_reduce(2 * ns, s->partials, s->nb, s->scratch, s->result, st);
+    e = launch_reduce(2 * ns, ns, s->partials, s->nb, s->scratch, s->result, st);
   if (e == cudaSuccess) e = adr_flux_launch(s, st);
-  double h[16] = {0};
+  double h[kResSlots] = {0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h, s->result, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -567,29 +563,35 @@ extern "C" lbm_status lbm_adr_run(lbm_adr_solver *s, int64_t nsteps,
   s->has_check = true;
   std::memset(info, 0, sizeof(*info));
   info->steps = s->steps;
-  int status_word = 0;
-  std::memcpy(&status_word, &h[15], sizeof(int));
-  if (status_word != 0) {
-    set_error("lbm_adr_run: a staged copy did not complete in time");
-    return LBM_ECUDA;
-  }
   bool finite = true;
   double r = 0.0;
   for (int k = 0; k < ns; ++k) {
     const double num = h[2 * k], den = h[2 * k + 1];
     finite = finite && std::isfinite(num) && std::isfinite(den) &&
-             std::isfinite(h[8 + k]);
+             std::isfinite(h[kResFlux + k]);
     if (den > 0) r = std::fmax(r, num / den);
-    info->flux[k] = h[8 + k];
+    info->flux[k] = h[kResFlux + k];
+    info->c_min[k] = h[2 * ns + k];
+    info->mass[k] = den;
   }
   info->residual = finite ? r : NAN;
-  info->converged = (finite && s->p.tol > 0 && r < s->p.tol) ? 1 : 0;
+  const bool negative = finite && adr_negative(&s->p, info->c_min);
+  info->converged = (finite && !negative && s->p.tol > 0 && r < s->p.tol) ? 1 : 0;
   if (ns >= 2) {
     double eps = 0.0;
     if (lbm_efficiency(info->flux, ns, &eps) == LBM_OK) info->eps = eps;
   }
   if (!finite) {
-    set_error("lbm_adr_run: non-finite concentration or flux");
+    set_error("lbm_adr_run: non-finite concentration or flux at step " +
+              std::to_string(s->steps));
+    return LBM_EUNSTABLE;
+  }
+  if (negative) {
+    double m = 0.0;
+    for (int k = 0; k < ns; ++k) m = std::fmin(m, info->c_min[k]);
+    set_error("lbm_adr_run: concentration " + std::to_string(m) +
+              " below -neg_tol at step " + std::to_string(s->steps) +
+              " (the scheme is losing stability: tau near 1/2?)");
     return LBM_EUNSTABLE;
   }
   return LBM_OK;
@@ -779,7 +781,7 @@ static AdjLayout adj_layout(const lbm_geometry *g, const lbm_adr_params *p) {
   l.buf = align256(ns * 9 * pl * compute_bytes(p->precision));
   l.partials = align256(static_cast<size_t>(gr.x) * gr.y * 2 * 8);
   l.scratch = align256(kReduceGrid * 2 * 8);
-  l.result = align256(64 * 8);
+  l.result = align256(kResSlots * 8);
   l.fiber = align256(4 * pl);
   l.total = 2 * l.buf + l.partials + l.scratch + l.result + l.fiber;
   return l;
@@ -864,12 +866,12 @@ extern "C" lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps,
 
   // forward outfluxes of the current state -> d eps / d N_s
   cudaError_t e = adr_flux_launch(s, st);
-  double h[16] = {0};
+  double h[kResSlots] = {0};
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h, s->result, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail("lbm_adr_adjoint(flux)", e);
-  double flux[3] = {h[8], h[9], h[10]};
+  double flux[3] = {h[kResFlux], h[kResFlux + 1], h[kResFlux + 2]};
   double dN[3];
   efficiency_sensitivity(flux, ns, dN);
   if (!std::isfinite(dN[0]) || !std::isfinite(dN[1]) || !std::isfinite(dN[2])) {
@@ -912,7 +914,7 @@ extern "C" lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps,
       cur ^= 1;
       ++steps;
     }
-    cudaError_t e2 = launch_reduce(2, partials, rows, scratch, result, st);
+    cudaError_t e2 = launch_reduce(2, 0, partials, rows, scratch, result, st);
     double r[2] = {0, 0};
     if (e2 == cudaSuccess)
       e2 = cudaMemcpyAsync(r, result, sizeof(r), cudaMemcpyDeviceToHost, st);
@@ -1009,9 +1011,6 @@ static __device__ __align__(256) double
 namespace lbm {
 namespace noalloc {
 
-static std::mutex g_mutex;
-static double *g_addr[256] = {};  // device address of the array, per device
-
 // Rows [b*256, b*256+256) of the plane x = xp: per species the sum over those
 // rows of sum_i c_ix g*_{s,i}, written to part[b*3 + s].  Every block writes
 // all three slots, so nothing has to start at zero.
@@ -1105,25 +1104,14 @@ extern "C" lbm_status lbm_adr_outflux_noalloc(lbm_adr_solver *s,
     return LBM_EINVAL;
   }
   if (lbm_status bs = bind_device(s->buf[0], "lbm_adr_outflux_noalloc")) return bs;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail("lbm_adr_outflux_noalloc", e);
-  if (dev < 0 || dev >= 256) {
-    set_error("lbm_adr_outflux_noalloc: device index out of range");
-    return LBM_EINVAL;
-  }
-  double *scratch = nullptr;
-  {
-    // first call on a device: look up the array's device address once
-    std::lock_guard<std::mutex> lock(noalloc::g_mutex);
-    if (!noalloc::g_addr[dev]) {
-      void *p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) return cuda_fail("lbm_adr_outflux_noalloc(setup)", e);
-      noalloc::g_addr[dev] = static_cast<double *>(p);
-    }
-    scratch = noalloc::g_addr[dev];
-  }
+  // The array's name is a host-side stand-in: its device address (on the
+  // device the solver's buffers live on, now current) is looked up on every
+  // call, so a context torn down and rebuilt (cudaDeviceReset) cannot leave
+  // a stale address behind.  The lookup allocates nothing.
+  void *sym = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&sym, g_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail("lbm_adr_outflux_noalloc(address)", e);
+  double *scratch = static_cast<double *>(sym);
   cudaStream_t st = as_stream(stream);
   const void *cur = s->buf[s->cur];
   const int ns = s->p.nspecies;

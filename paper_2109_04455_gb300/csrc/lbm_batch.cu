@@ -76,44 +76,50 @@ __global__ void __launch_bounds__(BX)
       }
     }
     __syncthreads();
-    T acc[2 * NS];
+    T acc[1][3 * NS];
 #pragma unroll
-    for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
+    for (int k = 0; k < 3 * NS; ++k) acc[0][k] = T(0);
     if (!(item & kChunkBit)) {
       const long long y = static_cast<long long>((item >> 24) & 0xffffff);
       const long long xb = static_cast<long long>(item & 0xffffff);
       const int x = static_cast<int>(xb * BX + threadIdx.x);
       const long long n = y * sa.nx_pad + x;
       const uint32_t lw = (x < sa.nx_pad) ? sa.links[n] : kSolidNode;
-      if (lw == 0u) adr_interior_node<P, NS, MODE>(sa, n, acc);
+      if (lw == 0u) adr_interior_node<P, NS, MODE>(sa, n, acc[0]);
     } else {
       const long long t =
           static_cast<long long>(item & ((1ull << 48) - 1)) + threadIdx.x;
       if (t < sa.nbnd) {
         const long long n = sa.bnodes[t];
         adr_general_node<P, NS, MODE>(sa, n, static_cast<int>(n % sa.nx_pad),
-                                      sa.links[n], acc);
+                                      sa.links[n], acc[0]);
       }
     }
-    if (MODE == kAdrCheck) block_sum_store<2 * NS, T>(acc, partials + w * (2 * NS));
+    if constexpr (MODE == kAdrCheck)
+      block_partials_store<2 * NS, NS, 1, BX, T>(acc, partials + w * (3 * NS));
   }
 }
 
-// out[i*K + k] = sum of partial rows [rows[2i], rows[2i+1]) (one block per
-// instance, fixed order).
-template <int K>
+// out[i*K + k] = fold of partial rows [rows[2i], rows[2i+1]) (one block per
+// instance, fixed order): sums of the first 2 NS components, minima of the
+// last NS.
+template <int NS>
 __global__ void __launch_bounds__(kReduceThreads)
     batch_reduce_kernel(const double *partials, const long long *rows,
                         double *out) {
+  constexpr int K = 3 * NS;
   const long long lo = rows[2 * blockIdx.x], hi = rows[2 * blockIdx.x + 1];
-  double acc[K];
+  double acc[1][K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (int k = 0; k < K; ++k) acc[0][k] = 0.0;
   for (long long b = lo + threadIdx.x; b < hi; b += blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] += partials[b * K + k];
+    for (int k = 0; k < K; ++k)
+      acc[0][k] = k < 2 * NS ? acc[0][k] + partials[b * K + k]
+                             : fmin(acc[0][k], partials[b * K + k]);
   }
-  block_sum_store<K, double>(acc, out + (long long)blockIdx.x * K);
+  block_partials_store<2 * NS, NS, 1, kReduceThreads, double>(
+      acc, out + (long long)blockIdx.x * K);
 }
 
 // Outflux of every instance on its plane (one block per instance), from the
@@ -221,7 +227,7 @@ struct lbm_batch {
   unsigned long long *d_work = nullptr;
   double *d_partials = nullptr;
   long long *d_rows = nullptr;
-  double *d_sums = nullptr;             // [count][2*ns]
+  double *d_sums = nullptr;             // [count][3*ns]: sums, minima
   double *d_flux = nullptr;             // [count][3]
   unsigned *d_step = nullptr;           // [2] step count, ping-pong
   long long max_items = 0;
@@ -242,6 +248,7 @@ struct lbm_batch {
   // captured chunk
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap = nullptr;
+  bool solved = false;                  // a solve has recorded concentrations
 };
 
 namespace {
@@ -276,9 +283,9 @@ BatchLayout batch_layout(int count, const lbm_geometry *const *geoms,
   for (int i = 0; i < count; ++i) items += items_of(geoms[i], 128);
   l.table = a256(sizeof(AdrArgs) * 2 * count);
   l.work = a256(8 * items);
-  l.partials = a256(8 * 2 * ns * items);
+  l.partials = a256(8 * 3 * ns * items);
   l.rows = a256(8 * 2 * count);
-  l.sums = a256(8 * 2 * ns * count);
+  l.sums = a256(8 * 3 * ns * count);
   l.flux = a256(8 * 3 * count);
   l.step = a256(2 * sizeof(unsigned));
   l.head = l.table + l.work + l.partials + l.rows + l.sums + l.flux + l.step;
@@ -339,9 +346,9 @@ cudaError_t flux_launch(lbm_batch *b, int parity, cudaStream_t st) {
 
 cudaError_t reduce_launch(lbm_batch *b, cudaStream_t st) {
   if (b->ns == 2)
-    batch_reduce_kernel<4><<<b->count, kReduceThreads, 0, st>>>(b->d_partials, b->d_rows, b->d_sums);
+    batch_reduce_kernel<2><<<b->count, kReduceThreads, 0, st>>>(b->d_partials, b->d_rows, b->d_sums);
   else
-    batch_reduce_kernel<6><<<b->count, kReduceThreads, 0, st>>>(b->d_partials, b->d_rows, b->d_sums);
+    batch_reduce_kernel<3><<<b->count, kReduceThreads, 0, st>>>(b->d_partials, b->d_rows, b->d_sums);
   return cudaGetLastError();
 }
 
@@ -646,10 +653,11 @@ extern "C" lbm_status lbm_batch_solve(lbm_batch *b, void *stream,
   }
   lbm_status s = init_states(b, st);
   if (s != LBM_OK) return s;
+  b->solved = true;
   std::fill(b->active.begin(), b->active.end(), 1);
   std::memset(infos, 0, sizeof(lbm_solve_info) * b->count);
   const int ns = b->ns;
-  std::vector<double> sums(2 * ns * b->count), flux(3 * b->count);
+  std::vector<double> sums(3 * ns * b->count), flux(3 * b->count);
   bool rebuild = true;
   lbm_status result = LBM_OK;
   while (true) {
@@ -678,30 +686,38 @@ extern "C" lbm_status lbm_batch_solve(lbm_batch *b, void *stream,
       b->steps[i] += b->check_every;
       lbm_solve_info &inf = infos[i];
       inf.steps = b->steps[i];
+      const lbm_adr_params &p = b->params[i];
+      const double *row = &sums[(size_t)i * 3 * ns];
       double r = 0.0;
       bool finite = true;
       for (int k = 0; k < ns; ++k) {
-        const double num = sums[(size_t)i * 2 * ns + 2 * k];
-        const double den = sums[(size_t)i * 2 * ns + 2 * k + 1];
+        const double num = row[2 * k], den = row[2 * k + 1];
         finite = finite && std::isfinite(num) && std::isfinite(den);
         if (den > 0) r = std::fmax(r, num / den);
         inf.flux[k] = flux[(size_t)i * 3 + k];
         finite = finite && std::isfinite(inf.flux[k]);
+        inf.c_min[k] = row[2 * ns + k];
+        inf.mass[k] = den;
       }
       inf.residual = finite ? r : NAN;
       double eps = 0.0;
       if (lbm_efficiency(inf.flux, ns, &eps) == LBM_OK) inf.eps = eps;
-      const lbm_adr_params &p = b->params[i];
-      const bool conv = finite && p.tol > 0 && r < p.tol;
+      const bool negative = finite && adr_negative(&p, inf.c_min);
+      const bool conv = finite && !negative && p.tol > 0 && r < p.tol;
       inf.converged = conv ? 1 : 0;
       if (!finite) {
         result = LBM_EUNSTABLE;
         set_error("lbm_batch_solve: non-finite sums in instance " + std::to_string(i));
+      } else if (negative) {
+        result = LBM_EUNSTABLE;
+        set_error("lbm_batch_solve: instance " + std::to_string(i) +
+                  " has a concentration below -neg_tol at step " +
+                  std::to_string(b->steps[i]));
       }
-      if (conv || !finite || b->steps[i] >= p.max_steps) {
+      if (conv || !finite || negative || b->steps[i] >= p.max_steps) {
         b->active[i] = 0;
         rebuild = true;
-        if (!conv && finite && p.tol > 0 && result == LBM_OK)
+        if (!conv && finite && !negative && p.tol > 0 && result == LBM_OK)
           result = LBM_ENOTCONVERGED;
       }
     }
@@ -719,5 +735,24 @@ extern "C" lbm_status lbm_batch_tuning(const lbm_batch *b, int32_t *tile,
   if (grid) *grid = static_cast<int32_t>(b->grid);
   if (ms_per_step)
     for (int k = 0; k < 8; ++k) ms_per_step[k] = b->tune_ms[k];
+  return LBM_OK;
+}
+
+extern "C" lbm_status lbm_batch_conc(const lbm_batch *b, int32_t index,
+                                     void *conc_out, void *stream) {
+  if (!b || !conc_out || index < 0 || index >= b->count) {
+    set_error("lbm_batch_conc: NULL argument or index outside the batch");
+    return LBM_EINVAL;
+  }
+  if (!b->solved) {
+    set_error("lbm_batch_conc: no solve has run on this batch");
+    return LBM_EINVAL;
+  }
+  const AdrArgs &a = b->table[2 * index];
+  const size_t bytes = static_cast<size_t>(b->ns) * static_cast<size_t>(a.plane) *
+                       comp_b(b->prec);
+  cudaError_t e = cudaMemcpyAsync(conc_out, a.cprev, bytes, cudaMemcpyDeviceToDevice,
+                                  static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return bfail("lbm_batch_conc", e);
   return LBM_OK;
 }

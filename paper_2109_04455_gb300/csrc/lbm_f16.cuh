@@ -21,35 +21,52 @@ namespace f16 {
 constexpr float kDown = 1.0f / 16384.0f, kUp = 16384.0f;
 __device__ __forceinline__ float w(int i) { return Lattice<float>::w(i); }
 // scaled population pulled from a source node: its stored deviation h plus
-// w_i times the source's scaled reference concentration rs = 2^14 R
-__device__ __forceinline__ float pull(int i, float h, float rs) {
-  return __fmaf_rn(w(i), rs, h);
+// w_i 2^14 times the source's reference concentration r (as stored, at
+// scale 1).  w_i 2^14 is exact, so this equals fma(w_i, 2^14 r, h) bit for
+// bit, without the multiply by 2^14.
+__device__ __forceinline__ float pull(int i, float h, float r) {
+  return __fmaf_rn(w(i) * kUp, r, h);
 }
-__device__ __forceinline__ float scaled_ref(__half r) {
-  return __fmul_rn(__half2float(r), kUp);
-}
-// equilibrium factors E_i(u) = w_i (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u)
+// equilibrium factors E_i(u) = w_i (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u),
+// built for each direction together with its opposite (c.u changes sign,
+// the even part w_i (1 + 4.5 (c.u)^2 - 1.5 u.u) is shared)
 __device__ __forceinline__ void eq(float ux, float uy, float (&E)[9]) {
   const float base = __fmaf_rn(-1.5f, __fmaf_rn(ux, ux, __fmul_rn(uy, uy)), 1.0f);
+  E[0] = __fmul_rn(w(0), base);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
+  for (int k = 0; k < 4; ++k) {
+    const int i = k < 2 ? k + 1 : k + 3;   // 1, 2, 5, 6
     const float cu = __fadd_rn(float(cx(i)) * ux, float(cy(i)) * uy);
-    E[i] = __fmul_rn(w(i), __fmaf_rn(__fmul_rn(4.5f, cu), cu, __fmaf_rn(3.0f, cu, base)));
+    const float even = __fmul_rn(w(i), __fmaf_rn(__fmul_rn(4.5f, cu), cu, base));
+    E[i] = __fmaf_rn(3.0f * w(i), cu, even);
+    E[opp(i)] = __fmaf_rn(-3.0f * w(i), cu, even);
   }
 }
+// C_s at scale 2^14: a pairwise sum (short dependency chains)
 __device__ __forceinline__ float sum9(const float (&g)[9]) {
-  float c = g[0];
-#pragma unroll
-  for (int i = 1; i < 9; ++i) c = __fadd_rn(c, g[i]);
-  return c;
+  const float a = __fadd_rn(__fadd_rn(g[0], g[1]), __fadd_rn(g[2], g[3]));
+  const float b = __fadd_rn(__fadd_rn(g[4], g[5]), __fadd_rn(g[6], g[7]));
+  return __fadd_rn(__fadd_rn(a, b), g[8]);
 }
-// value stored for population i: the BGK relaxation G + om (Cs E_i - G)
-// less w_i times the node's stored reference, all at scale 2^14 (cqs is
-// 2^14 times the half-rounded concentration)
-__device__ __forceinline__ float push(int i, float g, float cs, float e, float om,
-                                      float cqs) {
-  const float post = __fmaf_rn(om, __fmaf_rn(cs, e, -g), g);
-  return __fmaf_rn(-w(i), cqs, post);
+// Per node and species: keep = 1 - om, a = om C_s (scale 2^14), and w_i
+// times the node's stored reference (scale 2^14) for the three weights.
+struct PushK {
+  float keep, a, wq[3];
+};
+__device__ __forceinline__ PushK push_k(float om, float cs, float cqs) {
+  PushK k;
+  k.keep = __fsub_rn(1.0f, om);
+  k.a = __fmul_rn(om, cs);
+  k.wq[0] = __fmul_rn(w(0), cqs);
+  k.wq[1] = __fmul_rn(w(1), cqs);
+  k.wq[2] = __fmul_rn(w(5), cqs);
+  return k;
+}
+// value stored for population i: the BGK relaxation (1 - om) G + om C_s E_i
+// less w_i times the node's stored reference, all at scale 2^14: two FMAs
+__device__ __forceinline__ float push(int i, float g, float e, const PushK &k) {
+  const float wq = i == 0 ? k.wq[0] : (i < 5 ? k.wq[1] : k.wq[2]);
+  return __fmaf_rn(k.keep, g, __fmaf_rn(k.a, e, -wq));
 }
 
 // Rounding of a scaled population to half.  LBM_F16_SR = 1 (default):
@@ -116,7 +133,7 @@ __device__ __forceinline__ __half2 round_pair(float lo, float hi, uint32_t h,
 
 template <int NS, int MODE>
 __device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long long n,
-                                                      float (&acc)[2 * NS]) {
+                                                      float (&acc)[3 * NS]) {
   const long long np = a.nx_pad, plane = a.plane;
   const __half *__restrict__ src = static_cast<const __half *>(a.src);
   __half *__restrict__ dst = static_cast<__half *>(a.dst);
@@ -128,7 +145,7 @@ __device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long lon
     for (int i = 0; i < 9; ++i) {
       const long long m = n - (cy(i) * np + cx(i));
       g[s][i] = f16::pull(i, __half2float(src[(long long)(s * 9 + i) * plane + m]),
-                          f16::scaled_ref(a.rsrc[s * plane + m]));
+                          __half2float(a.rsrc[s * plane + m]));
     }
   }
   float *__restrict__ cp = static_cast<float *>(a.cprev);
@@ -147,18 +164,18 @@ __device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long lon
     const float c = __fmul_rn(cs, f16::kDown);
     const float cqs = __fmul_rn(ref_round(c), f16::kUp);
     a.rdst[s * plane + n] = __float2half_rn(c);
+    const f16::PushK k = f16::push_k(a.fomega[s], cs, cqs);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       // rounded as one half of its pair, with the pair's random bits
-      const float v = f16::push(i, g[s][i], cs, E[i], a.fomega[s], cqs);
+      const float v = f16::push(i, g[s][i], E[i], k);
       const __half2 r2 = f16::round_pair(odd ? 0.0f : v, odd ? v : 0.0f, h,
                                          s * 9 + i);
       dst[(long long)(s * 9 + i) * plane + n] = odd ? __high2half(r2)
                                                     : __low2half(r2);
     }
     if (MODE == kAdrCheck) {
-      acc[2 * s] += fabsf(c - prev[s]);
-      acc[2 * s + 1] += fabsf(c);
+      check_add<NS, float>(acc, s, c, prev[s]);
       cp[s * plane + n] = c;
     }
   }
@@ -188,9 +205,9 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
   uint2 lw = make_uint2(kSolidNode, kSolidNode);
   if (x0 < a.nx_pad) lw = *reinterpret_cast<const uint2 *>(a.links + n0);
   const bool in0 = lw.x == 0u, in1 = lw.y == 0u;
-  float acc[2 * NS];
+  float acc[2][3 * NS];   // check-step values of node x0 and of node x0 + 1
 #pragma unroll
-  for (int k = 0; k < 2 * NS; ++k) acc[k] = 0.0f;
+  for (int k = 0; k < 3 * NS; ++k) acc[0][k] = acc[1][k] = 0.0f;
   if (in0 || in1) {
     const __half *__restrict__ src = static_cast<const __half *>(a.src);
     __half *__restrict__ dst = static_cast<__half *>(a.dst);
@@ -232,15 +249,16 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
     const uint32_t hp = f16::pair_hash(n0 >> 1, a.step);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      // scaled references of the source columns x0 - 1 .. x0 + 2, rows
+      // references of the source columns x0 - 1 .. x0 + 2, rows
       // y - 1 .. y + 1 (the left / right column only where it is read)
       float rs[3][4];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        rs[r][0] = f16::scaled_ref(__high2half(rl[s][r]));
-        rs[r][1] = f16::scaled_ref(__low2half(rc[s][r]));
-        rs[r][2] = f16::scaled_ref(__high2half(rc[s][r]));
-        rs[r][3] = f16::scaled_ref(__low2half(rr[s][r]));
+        const float2 c2 = __half22float2(rc[s][r]);
+        rs[r][0] = __high2float(rl[s][r]);
+        rs[r][1] = c2.x;
+        rs[r][2] = c2.y;
+        rs[r][3] = __low2float(rr[s][r]);
       }
       float g0[9], g1[9];
 #pragma unroll
@@ -266,6 +284,8 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
       const float cq0 = __fmul_rn(ref_round(c0), f16::kUp);
       const float cq1 = __fmul_rn(ref_round(c1), f16::kUp);
       const float om = a.fomega[s];
+      const f16::PushK k0 = f16::push_k(om, cs0, cq0);
+      const f16::PushK k1 = f16::push_k(om, cs1, cq1);
       __half *o = dst + (long long)s * 9 * plane + n0;
       __half *ro = a.rdst + (long long)s * plane + n0;
       float *co = cp + s * plane + n0;
@@ -273,8 +293,8 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
 #pragma unroll
         for (int i = 0; i < 9; ++i)
           *reinterpret_cast<__half2 *>(o + (long long)i * plane) = f16::round_pair(
-              f16::push(i, g0[i], cs0, E0[i], om, cq0),
-              f16::push(i, g1[i], cs1, E1[i], om, cq1), hp, s * 9 + i);
+              f16::push(i, g0[i], E0[i], k0), f16::push(i, g1[i], E1[i], k1), hp,
+              s * 9 + i);
         *reinterpret_cast<__half2 *>(ro) = __floats2half2_rn(c0, c1);
         if (MODE == kAdrCheck) *reinterpret_cast<float2 *>(co) = make_float2(c0, c1);
       } else {
@@ -282,8 +302,8 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
           const __half2 r2 = f16::round_pair(
-              in0 ? f16::push(i, g0[i], cs0, E0[i], om, cq0) : 0.0f,
-              in1 ? f16::push(i, g1[i], cs1, E1[i], om, cq1) : 0.0f, hp, s * 9 + i);
+              in0 ? f16::push(i, g0[i], E0[i], k0) : 0.0f,
+              in1 ? f16::push(i, g1[i], E1[i], k1) : 0.0f, hp, s * 9 + i);
           if (in0) o[(long long)i * plane] = __low2half(r2);
           if (in1) o[(long long)i * plane + 1] = __high2half(r2);
         }
@@ -295,20 +315,15 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
         }
       }
       if (MODE == kAdrCheck) {
-        if (in0) {
-          acc[2 * s] += fabsf(c0 - prev[s].x);
-          acc[2 * s + 1] += fabsf(c0);
-        }
-        if (in1) {
-          acc[2 * s] += fabsf(c1 - prev[s].y);
-          acc[2 * s + 1] += fabsf(c1);
-        }
+        if (in0) check_add<NS, float>(acc[0], s, c0, prev[s].x);
+        if (in1) check_add<NS, float>(acc[1], s, c1, prev[s].y);
       }
     }
   }
-  if (MODE == kAdrCheck) {
+  if constexpr (MODE == kAdrCheck) {
     const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-    block_sum_store<2 * NS, float>(acc, a.partials + b * (2 * NS));
+    block_partials_store<2 * NS, NS, 2, kPairThreads, float>(
+        acc, a.partials + b * (3 * NS));
   }
 }
 

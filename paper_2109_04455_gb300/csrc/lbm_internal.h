@@ -21,6 +21,9 @@ enum LinkType : uint32_t {
   kCat = 3,     // fiber node with a rate: bounce-back + Dawson source
   kInlet = 4,   // beyond x = -1/2
   kOutlet = 5,  // beyond x = nx - 1/2
+  kPeriodic = 6,  // fluid node across a periodic edge: plain streaming from
+                  // the wrapped node (a solid node across the edge is
+                  // kInert / kCat, with the wrapped node's rates)
 };
 constexpr uint32_t kSolidNode = 0xFFFFFFFFu;
 
@@ -34,6 +37,19 @@ inline size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
 void set_error(const std::string &msg);
 
+// True when some species' most negative concentration c_min[s] is below
+// -neg_tol * max(1, c_in) (neg_tol 0 selects 0.1, < 0 disables the test).
+inline bool adr_negative(const lbm_adr_params *p, const double *c_min) {
+  if (p->neg_tol < 0) return false;
+  const double tol = p->neg_tol > 0 ? p->neg_tol : 0.1;
+  double scale = 1.0;
+  for (int s = 0; s < p->nspecies; ++s)
+    scale = p->c_in[s] > scale ? p->c_in[s] : scale;
+  for (int s = 0; s < p->nspecies; ++s)
+    if (c_min[s] < -tol * scale) return true;
+  return false;
+}
+
 }  // namespace lbm
 
 struct lbm_geometry {
@@ -45,6 +61,7 @@ struct lbm_geometry {
   std::vector<long long> bnodes;  // fluid nodes with a non-zero link word
   std::vector<int32_t> fiber;     // [ny][nx_pad] owning fiber, -1 elsewhere
   int32_t nfibers = 0;
+  int32_t periodic = 0;           // LBM_PERIODIC_X | LBM_PERIODIC_Y
   double k1 = 0.0, k2 = 0.0;
   // device copies (borrowed from the caller's workspace after upload)
   const uint32_t *d_links = nullptr;

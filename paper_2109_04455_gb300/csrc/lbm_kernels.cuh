@@ -106,14 +106,26 @@ __device__ __forceinline__ constexpr int opp(int i) {
 __device__ __forceinline__ uint32_t nib(uint32_t word, int j) {
   return (word >> (4 * (j - 1))) & 0xFu;
 }
+// Index of the neighbour x + c_j of the node (x, y) (plane index
+// y * np + x), wrapped around a periodic edge; for a neighbour inside the
+// lattice it is the plain shift.  Used on boundary nodes only (kPeriodic
+// pulls, rates of catalytic links).
+__device__ __forceinline__ long long neighbour(int x, int y, int j, int nx,
+                                               int ny, long long np) {
+  int tx = x + cx(j), ty = y + cy(j);
+  tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
+  ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
+  return (long long)ty * np + tx;
+}
+
+__device__ __forceinline__ float absT(float x) { return fabsf(x); }
+__device__ __forceinline__ double absT(double x) { return fabs(x); }
 
 // ---------------------------------------------------------------------------
-// deterministic block reduction of K values, stored by threads 0..K-1 (one
-// component each) to dst[0..K).  The block-level sums stay in the value type
-// A (float on the float paths): this part's FP64 pipe is narrow, and a chain
-// of double additions at the end of every block held each block's slot long
-// enough to multiply the time of a check step.  The grid-level sums of these
-// partials are taken in double by reduce_partials_kernel.
+// deterministic block sum of K values in the value type A, stored by threads
+// 0..K-1 (one component each) to dst[0..K): used in double for the outflux
+// and for the adjoint's convergence measure.  (The forward check steps use
+// block_partials_store below, which sums in double whatever the precision.)
 // ---------------------------------------------------------------------------
 template <int K, typename A>
 __device__ __forceinline__ void block_sum_store(const A (&v)[K], double *dst) {
@@ -137,6 +149,60 @@ __device__ __forceinline__ void block_sum_store(const A (&v)[K], double *dst) {
     for (int i = 0; i < nw; ++i) s += red[i][threadIdx.x];
     dst[threadIdx.x] = double(s);
   }
+}
+
+// Check-step partials of one block, accumulated in double.  Each of the BX
+// threads passes the values of NPER nodes, v[NPER][KS + KM] (zeros for a
+// thread or node without a fluid node): the first KS components are summed,
+// the last KM reduced by minimum (a minimum starts at 0, so it is that of
+// min(value, 0)).  The values are staged in shared memory, one row per
+// component; warp w then reduces components w, w + BX/32, ...: its lanes add
+// the component's values at a stride of 32 in double, and the 32 lane sums
+// are folded by double shuffles.  Every per-node value enters a double sum,
+// so a block partial carries no single-precision rounding; the fixed order
+// makes it deterministic.
+template <int KS, int KM, int NPER, int BX, typename A>
+__device__ __forceinline__ void block_partials_store(const A (&v)[NPER][KS + KM],
+                                                     double *dst) {
+  constexpr int K = KS + KM;
+  constexpr int NV = BX * NPER;
+  static_assert(BX % 32 == 0, "whole warps");
+  __shared__ A stage[K][NV];
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int p = 0; p < NPER; ++p) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) stage[k][p * BX + t] = v[p][k];
+  }
+  __syncthreads();
+  const int lane = t & 31, warp = t >> 5;
+  for (int k = warp; k < K; k += BX / 32) {
+    double r = 0.0;
+    if (k < KS) {
+#pragma unroll 4
+      for (int j = lane; j < NV; j += 32) r += double(stage[k][j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    } else {
+      A m = A(0);
+#pragma unroll 4
+      for (int j = lane; j < NV; j += 32) m = stage[k][j] < m ? stage[k][j] : m;
+      r = double(m);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r = fmin(r, __shfl_down_sync(0xffffffffu, r, o));
+    }
+    if (lane == 0) dst[k] = r;
+  }
+}
+
+// Per-node contribution of species s to a check step's partials (layout
+// [2 NS sums | NS minima]): |C(t) - C(t-1)|, |C(t)|, and C(t) for the most
+// negative concentration.
+template <int NS, typename T>
+__device__ __forceinline__ void check_add(T (&acc)[3 * NS], int s, T c, T prev) {
+  acc[2 * s] += absT(c - prev);
+  acc[2 * s + 1] += absT(c);
+  acc[2 * NS + s] = c < acc[2 * NS + s] ? c : acc[2 * NS + s];
 }
 
 // two-wide vector of a storage / compute type
@@ -172,8 +238,6 @@ __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <>
 __device__ __forceinline__ float pick<float>(double, float f) { return f; }
 
-__device__ __forceinline__ float absT(float x) { return fabsf(x); }
-__device__ __forceinline__ double absT(double x) { return fabs(x); }
 
 // ---------------------------------------------------------------------------
 // ADR
@@ -185,13 +249,12 @@ struct AdrArgs {
   const double *kab, *kbc;  // [plane]
   const void *u;            // T [2][plane]
   void *cprev;              // T [ns][plane]     (check steps)
-  double *partials;         // [rows][2*ns]      (check steps)
+  double *partials;         // [rows][3*ns]      (check steps)
   const long long *bnodes;  // boundary fluid nodes (link word != 0)
   long long nbnd;           // number of boundary nodes
   long long part_off;       // first partial row of the boundary kernel
   long long plane;          // ny * nx_pad
   int nx, ny, nx_pad;
-  int *status;              // device word: non-zero after a failed wait
   int abb_all;              // anti-bounce-back inlet for every species
   int nodewise;             // every population of a reactive node reacts
   unsigned step;            // steps done before this one (rounding seed)
@@ -317,7 +380,7 @@ __device__ __forceinline__ void adr_boundary(const AdrArgs &a, int s,
 #pragma unroll
   for (int i = 1; i < 9; ++i) {
     const uint32_t t = nib(lw, opp(i));
-    if (t == kFluid) continue;
+    if (t == kFluid || t == kPeriodic) continue;   // pulled already
     const T back = adr_ld<P>(a, s, opp(i), n);
     if (t == kInlet) {
       g[i] = (s == 0 || a.abb_all)
@@ -340,6 +403,7 @@ __device__ __forceinline__ void adr_boundary(const AdrArgs &a, int s,
 template <class P, int NS>
 __device__ __forceinline__ typename P::T adr_collide(const AdrArgs &a, int s,
                                                      uint32_t lw, long long n,
+                                                     int x, int y,
                                                      const typename P::T (&E)[9],
                                                      typename P::T (&g)[9],
                                                      typename P::T (&C)[NS]) {
@@ -358,7 +422,7 @@ __device__ __forceinline__ typename P::T adr_collide(const AdrArgs &a, int s,
 #pragma unroll
     for (int j = 1; j < 9; ++j) {
       if (nib(lw, j) != kCat) continue;
-      const long long m = n + cy(j) * np + cx(j);
+      const long long m = neighbour(x, y, j, a.nx, a.ny, np);
       sa += T(a.kab[m]);
       sb += T(a.kbc[m]);
       ++ncat;
@@ -384,7 +448,7 @@ __device__ __forceinline__ typename P::T adr_collide(const AdrArgs &a, int s,
 #pragma unroll
     for (int j = 1; j < 9; ++j) {
       if (nib(lw, j) != kCat) continue;
-      const long long m = n + cy(j) * np + cx(j);
+      const long long m = neighbour(x, y, j, a.nx, a.ny, np);
       const T wj = Lattice<T>::w(j);
       if (s == 0) {
         g[j] -= T(a.kab[m]) * wj * C[0];
@@ -405,12 +469,13 @@ __device__ __forceinline__ typename P::T adr_collide(const AdrArgs &a, int s,
 template <class P, int NS, int MODE>
 __device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
                                                  int x, uint32_t lw,
-                                                 typename P::T (&acc)[2 * NS]) {
+                                                 typename P::T (&acc)[3 * NS]) {
   using S = typename P::S;
   using T = typename P::T;
   const long long plane = a.plane;
   S *__restrict__ dst = static_cast<S *>(a.dst);
   const long long np = (long long)a.nx_pad;
+  const int y = lw != 0u ? static_cast<int>(n / np) : 0;
   T E[9];
   adr_eq<P>(a, n, E);
   T C[NS];
@@ -424,13 +489,17 @@ __device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
     } else {
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        // pull from x - c_i when that node is fluid (always for lw == 0)
-        if (i == 0 || lw == 0u || nib(lw, opp(i)) == kFluid)
+        // pull from x - c_i when that node is fluid (always for lw == 0),
+        // from the wrapped node across a periodic edge
+        const uint32_t t = (i == 0 || lw == 0u) ? (uint32_t)kFluid : nib(lw, opp(i));
+        if (t == kFluid)
           g[i] = adr_ld<P>(a, s, i, n - (cy(i) * np + cx(i)));
+        else if (t == kPeriodic)
+          g[i] = adr_ld<P>(a, s, i, neighbour(x, y, opp(i), a.nx, a.ny, np));
       }
       if (lw != 0u) adr_boundary<P>(a, s, lw, n, x, g);
     }
-    const T c = adr_collide<P, NS>(a, s, lw, n, E, g, C);
+    const T c = adr_collide<P, NS>(a, s, lw, n, x, y, E, g, C);
     T cq = c;   // the reference stored with the populations (half path)
     if constexpr (P::kDev) {
       cq = ref_round(c);
@@ -441,8 +510,7 @@ __device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
       dst[(long long)(s * 9 + i) * plane + n] = P::store(g[i] - adr_unref<P>(i, cq));
     if (MODE == kAdrCheck) {
       T *cp = static_cast<T *>(a.cprev);
-      acc[2 * s] += absT(c - cp[s * plane + n]);
-      acc[2 * s + 1] += absT(c);
+      check_add<NS, T>(acc, s, c, cp[s * plane + n]);
       cp[s * plane + n] = c;
     }
   }
@@ -459,7 +527,7 @@ namespace lbm {
 // independent loads in flight.
 template <class P, int NS, int MODE>
 __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
-                                                  typename P::T (&acc)[2 * NS]) {
+                                                  typename P::T (&acc)[3 * NS]) {
   using S = typename P::S;
   using T = typename P::T;
   if constexpr (P::kDev) {
@@ -499,8 +567,7 @@ __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
       dst[(long long)(s * 9 + i) * plane + n] =
           P::store(g[s][i] + om * (c * E[i] - g[s][i]));
     if (MODE == kAdrCheck) {
-      acc[2 * s] += absT(c - prev[s]);
-      acc[2 * s + 1] += absT(c);
+      check_add<NS, T>(acc, s, c, prev[s]);
       cp[s * plane + n] = c;
     }
   }
@@ -527,14 +594,14 @@ __global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
     n = (long long)blockIdx.y * a.nx_pad + x;
     lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
   }
-  T acc[2 * NS];
+  T acc[1][3 * NS];
 #pragma unroll
-  for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
-  if (lw != kSolidNode) adr_general_node<P, NS, MODE>(a, n, x, lw, acc);
-  if (MODE == kAdrCheck) {
+  for (int k = 0; k < 3 * NS; ++k) acc[0][k] = T(0);
+  if (lw != kSolidNode) adr_general_node<P, NS, MODE>(a, n, x, lw, acc[0]);
+  if constexpr (MODE == kAdrCheck) {
     const long long b = LIST ? a.part_off + blockIdx.x
                              : (long long)blockIdx.y * gridDim.x + blockIdx.x;
-    block_sum_store<2 * NS, T>(acc, a.partials + b * (2 * NS));
+    block_partials_store<2 * NS, NS, 1, kBlockX, T>(acc, a.partials + b * (3 * NS));
   }
 }
 
@@ -548,16 +615,16 @@ __global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
   const int x = blockIdx.x * kBlockX + threadIdx.x;
   const long long n = (long long)blockIdx.y * a.nx_pad + x;
   const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
-  T acc[2 * NS];
+  T acc[1][3 * NS];
 #pragma unroll
-  for (int k = 0; k < 2 * NS; ++k) acc[k] = T(0);
+  for (int k = 0; k < 3 * NS; ++k) acc[0][k] = T(0);
   // (half storage: the references of the nine source nodes are read next
   // to the populations; gathering them with warp shuffles instead measured
   // slower, the shuffles keep the population loads from being issued early)
-  if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc);
-  if (MODE == kAdrCheck) {
+  if (lw == 0u) adr_interior_node<P, NS, MODE>(a, n, acc[0]);
+  if constexpr (MODE == kAdrCheck) {
     const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-    block_sum_store<2 * NS, T>(acc, a.partials + b * (2 * NS));
+    block_partials_store<2 * NS, NS, 1, kBlockX, T>(acc, a.partials + b * (3 * NS));
   }
 }
 
@@ -593,24 +660,29 @@ __global__ void __launch_bounds__(kReduceThreads)
   block_sum_store<NS, double>(acc, out);
 }
 
-// Sum rows of K partials in a fixed order.  Block b of the grid adds the
-// rows [b*chunk, (b+1)*chunk) into out[b*K + k]; a second launch with one
-// block folds those.  Deterministic for a fixed grid.
-template <int K>
+// Fold rows of KS + KM partials in a fixed order (sums of the first KS
+// components, minima of the last KM).  Block b of the grid folds the rows
+// [b*chunk, (b+1)*chunk) into out[b*K + k]; a second launch with one block
+// folds those.  Deterministic for a fixed grid.
+template <int KS, int KM>
 __global__ void __launch_bounds__(kReduceThreads)
     reduce_partials_kernel(const double *partials, long long nb, long long chunk,
                            double *out) {
-  double acc[K];
+  constexpr int K = KS + KM;
+  double acc[1][K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) acc[k] = 0.0;
+  for (int k = 0; k < K; ++k) acc[0][k] = 0.0;
   const long long lo = (long long)blockIdx.x * chunk;
   long long hi = lo + chunk;
   if (hi > nb) hi = nb;
   for (long long b = lo + threadIdx.x; b < hi; b += blockDim.x) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] += partials[b * K + k];
+    for (int k = 0; k < K; ++k)
+      acc[0][k] = k < KS ? acc[0][k] + partials[b * K + k]
+                         : fmin(acc[0][k], partials[b * K + k]);
   }
-  block_sum_store<K, double>(acc, out + (long long)blockIdx.x * K);
+  block_partials_store<KS, KM, 1, kReduceThreads, double>(
+      acc, out + (long long)blockIdx.x * K);
 }
 
 }  // namespace lbm
@@ -645,7 +717,7 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
   const long long n = (long long)y * a.nx_pad + x;
   const long long plane = a.plane;
   const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
-  T acc[2] = {T(0), T(0)};
+  T acc[1][2] = {{T(0), T(0)}};
   T *U = static_cast<T *>(a.u);
 
   if (lw != kSolidNode) {
@@ -693,6 +765,8 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
         const uint32_t t = nib(lw, opp(i));
         if (t == kFluid) {
           f[i] = ld(i, n - (cy(i) * np + cx(i)));
+        } else if (t == kPeriodic) {
+          f[i] = ld(i, neighbour(x, y, opp(i), a.nx, a.ny, np));
         } else if (t == kInlet) {
           // velocity bounce-back, rho_w = 1, u_w = (u_in(y), 0)
           f[i] = ld(opp(i), n) + T(6) * Lattice<T>::w(i) * T(cx(i)) * uin;
@@ -727,8 +801,8 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
     }
     if (MODE == kFlowU || MODE == kFlowCheck) {
       if (MODE == kFlowCheck) {
-        acc[0] = absT(ux - U[n]) + absT(uy - U[plane + n]);
-        acc[1] = absT(ux) + absT(uy);
+        acc[0][0] = absT(ux - U[n]) + absT(uy - U[plane + n]);
+        acc[0][1] = absT(ux) + absT(uy);
       }
       U[n] = ux;
       U[plane + n] = uy;
@@ -738,9 +812,9 @@ __global__ void __launch_bounds__(kBlockX) flow_kernel(const FlowArgs a) {
     U[plane + n] = T(0);
   }
 
-  if (MODE == kFlowCheck) {
+  if constexpr (MODE == kFlowCheck) {
     const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-    block_sum_store<2, T>(acc, a.partials + b * 2);
+    block_partials_store<2, 0, 1, kBlockX, T>(acc, a.partials + b * 2);
   }
 }
 
@@ -802,10 +876,17 @@ cudaError_t launch_adjoint_grad(int ns, const AdjArgs &a, const long long *bnode
                                 double *dkbc, const int32_t *fiber, double *dw,
                                 double k1, double k2, cudaStream_t st);
 
-// Two-level deterministic sum of nb rows of k partials into out[0..k);
-// scratch holds kReduceGrid * k doubles.
+// Two-level deterministic fold of nb rows of ks + km partials (ks sums, km
+// minima) into out[0..ks+km); scratch holds kReduceGrid * (ks + km)
+// doubles.  (ks, km) is (2, 0) (flow and adjoint residuals) or
+// (2 ns, ns) (ADR check steps).
 constexpr int kReduceGrid = 256;
-cudaError_t launch_reduce(int k, const double *partials, long long nb,
+cudaError_t launch_reduce(int ks, int km, const double *partials, long long nb,
                           double *scratch, double *out, cudaStream_t st);
+
+// Slots of a solver's result buffer: the folded check partials
+// [2 ns sums | ns minima] from 0, the outfluxes from kResFlux.
+constexpr int kResFlux = 16;
+constexpr int kResSlots = 24;
 
 }  // namespace lbm

@@ -3,45 +3,12 @@
 // the kernel variants compile in parallel.
 #pragma once
 
-#include <mutex>
-
 #include "lbm_kernels.cuh"
-#include "lbm_tma.cuh"
 
 namespace lbm {
 
-// Persistent grid of the TMA-staged step: resident blocks per SM x SMs of
-// the current device (the shared-memory limit is raised once per kernel).
-template <class P, int NS, int MODE>
-static unsigned tma_grid(long long ntiles) {
-  using L = TmaLayout<P, NS>;
-  static std::once_flag once;
-  static int per_sm = 1;
-  std::call_once(once, [] {
-    cudaFuncSetAttribute(adr_tma_kernel<P, NS, MODE>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(L::kBytes));
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &nb, adr_tma_kernel<P, NS, MODE>, kBlockX, L::kBytes);
-    per_sm = nb > 0 ? nb : 1;
-  });
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long g = static_cast<long long>(per_sm) * sms;
-  return static_cast<unsigned>(g < ntiles ? g : (ntiles > 0 ? ntiles : 1));
-}
-
 template <class P, int NS, int MODE>
 static void launch_bulk(const AdrArgs &a, dim3 bg, cudaStream_t st) {
-  if (adr_uses_tma<P>() && a.status != nullptr) {
-    using L = TmaLayout<P, NS>;
-    const long long ntiles = static_cast<long long>(bg.x) * bg.y;
-    adr_tma_kernel<P, NS, MODE>
-        <<<tma_grid<P, NS, MODE>(ntiles), kBlockX, L::kBytes, st>>>(a, a.status);
-    return;
-  }
   if constexpr (P::kDev && LBM_ADR_PAIR_F16)
     adr_bulk_pair_kernel<NS, MODE><<<bg, dim3(kPairThreads), 0, st>>>(a);
   else

@@ -308,5 +308,30 @@ def sweep_instance(i: int, n_pe: int = 8, n_da: int = 8) -> Workload:
                     da1=da, da2=da, r_ref=8.0)
 
 
+def noflow_box(kind: str, da: float, n: int = 300, xi: float = 100.0,
+               tau: float = 1.0) -> Workload:
+    """Pure-diffusion cascade of Sec. IV.B: an n x n box, periodic in both
+    directions, filled with A, no flow.  kind "pair": an A->B and a B->C
+    fiber of R = 5 on the box's centre line, their surfaces xi apart;
+    kind "side_by_side": one R = 10 fiber carrying both catalysts (A->B on
+    the half facing -x, B->C on the other), the same total surface.  With no
+    flow Pe is not defined: D follows from tau (the paper's tau = 1,
+    D = 1/6) and k = Da D / R^2 from each geometry's own R."""
+    d = (tau - 0.5) / 3.0
+    if kind == "pair":
+        r = 5.0
+        x1 = n / 2.0 - r - xi / 2.0
+        fib = fiber_table([[x1, n / 2.0, r, 1.0, 0.0, -1.0],
+                           [x1 + 2.0 * r + xi, n / 2.0, r, 2.0, 0.0, -1.0]])
+    elif kind == "side_by_side":
+        r = 10.0
+        fib = fiber_table([[n / 2.0, n / 2.0, r, 3.0, math.pi, -1.0]])
+    else:
+        raise ValueError(kind)
+    pe = 0.05 * r / d          # placeholder u0 = 0.05: only D matters here
+    return Workload(f"noflow_{kind}_da{da:g}", n, n, fib, 3, pe=pe, da1=da,
+                    da2=da, r_ref=r)
+
+
 def empty_channel(nx: int, ny: int) -> np.ndarray:
     return np.zeros((0, 6), dtype=np.float64)

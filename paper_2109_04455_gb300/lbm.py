@@ -25,6 +25,8 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ENOTCONVERGED, \
 LBM_F64, LBM_F32, LBM_F16DEV = range(3)
 LBM_ADR_INLET_ABB_ALL = 1
 LBM_ADR_NODEWISE = 2
+LBM_PERIODIC_X = 1
+LBM_PERIODIC_Y = 2
 PRECISIONS = {"f64": LBM_F64, "f32": LBM_F32, "f16dev": LBM_F16DEV}
 
 _STATUS = {LBM_EINVAL: "EINVAL", LBM_ENOMEM: "ENOMEM", LBM_ECUDA: "ECUDA",
@@ -40,12 +42,15 @@ class LBMError(RuntimeError):
 class lbm_solve_info(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("residual", ctypes.c_double),
                 ("converged", ctypes.c_int32),
-                ("flux", ctypes.c_double * 3), ("eps", ctypes.c_double)]
+                ("flux", ctypes.c_double * 3), ("eps", ctypes.c_double),
+                ("c_min", ctypes.c_double * 3), ("mass", ctypes.c_double * 3)]
 
     def as_dict(self):
         return dict(steps=int(self.steps), residual=float(self.residual),
                     converged=bool(self.converged),
-                    flux=[float(v) for v in self.flux], eps=float(self.eps))
+                    flux=[float(v) for v in self.flux], eps=float(self.eps),
+                    c_min=[float(v) for v in self.c_min],
+                    mass=[float(v) for v in self.mass])
 
 
 class lbm_flow_params(ctypes.Structure):
@@ -60,7 +65,30 @@ class lbm_adr_params(ctypes.Structure):
                 ("tau", ctypes.c_double * 3), ("c_in", ctypes.c_double * 3),
                 ("max_steps", ctypes.c_int64), ("tol", ctypes.c_double),
                 ("check_every", ctypes.c_int32), ("x_plane", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("neg_tol", ctypes.c_double)]
+
+
+class lbm_rwpt_params(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_double), ("dt", ctypes.c_double),
+                ("delta", ctypes.c_double), ("density", ctypes.c_double),
+                ("radius_offset", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("nspecies", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class lbm_rwpt_info(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("window_steps", ctypes.c_int64),
+                ("alive", ctypes.c_int64), ("out", ctypes.c_int64 * 3),
+                ("eps", ctypes.c_double), ("overflow", ctypes.c_int32)]
+
+    def as_dict(self):
+        return dict(steps=int(self.steps),
+                    window_steps=int(self.window_steps),
+                    alive=int(self.alive), out=[int(v) for v in self.out],
+                    eps=float(self.eps), overflow=bool(self.overflow))
+
+
+LBM_RWPT_PERIODIC = 1
+LBM_RWPT_HOMOGENEOUS = 2
 
 
 # name -> (restype, argtypes)
@@ -74,6 +102,7 @@ _SIGS = {
     "lbm_geometry_info": (ctypes.c_int, [_P, _P, _P]),
     "lbm_geometry_fields": (ctypes.c_int, [_P, _P, _P, _P]),
     "lbm_geometry_set_rates": (ctypes.c_int, [_P, _P, _P]),
+    "lbm_geometry_set_periodic": (ctypes.c_int, [_P, ctypes.c_int32]),
     "lbm_adr_state_bytes": (ctypes.c_size_t, [_P]),
     "lbm_adr_state_save": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
     "lbm_adr_state_load": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P]),
@@ -99,6 +128,19 @@ _SIGS = {
     "lbm_batch_tune": (ctypes.c_int, [_P, _P, _P, _P]),
     "lbm_batch_tuning": (ctypes.c_int, [_P, _P, _P, _P]),
     "lbm_batch_solve": (ctypes.c_int, [_P, _P, _P]),
+    "lbm_batch_conc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "lbm_rwpt_ws_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int32]),
+    "lbm_rwpt_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P,
+                                       ctypes.c_int32, ctypes.c_double,
+                                       ctypes.c_double, _P, _P,
+                                       ctypes.c_int64, _P, ctypes.c_size_t,
+                                       _P]),
+    "lbm_rwpt_destroy": (None, [_P]),
+    "lbm_rwpt_init": (ctypes.c_int, [_P, _P]),
+    "lbm_rwpt_run": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P]),
+    "lbm_rwpt_reset_counts": (ctypes.c_int, [_P, _P]),
+    "lbm_rwpt_particles": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P,
+                                          _P, _P]),
     "lbm_adr_adjoint_ws_bytes": (ctypes.c_size_t, [_P, _P]),
     "lbm_adr_adjoint": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double,
                                        ctypes.c_int32, _P, ctypes.c_size_t,
@@ -201,6 +243,13 @@ class Geometry:
                            for a in arrs]))
         return self
 
+    def set_periodic(self, flags: int):
+        """lbm_geometry_set_periodic: LBM_PERIODIC_X | LBM_PERIODIC_Y joins
+        those edges (0: inlet, outlet and walls).  Call upload() again
+        before the next solve."""
+        _check(load().lbm_geometry_set_periodic(self.handle, int(flags)))
+        return self
+
     def upload(self, device="cuda", stream=None):
         import torch
         nbytes = self.ws_bytes()
@@ -264,13 +313,16 @@ def lbm_flow_solve(geom: Geometry, tau: float, u0: float, max_steps: int,
 def adr_params(nspecies: int, tau, c_in=(1.0, 0.0, 0.0),
                precision: int = LBM_F64, max_steps: int = 0, tol: float = 0.0,
                check_every: int = 100, x_plane: int = -1,
-               flags: int = 0) -> lbm_adr_params:
+               flags: int = 0, neg_tol: float = 0.0) -> lbm_adr_params:
+    """ADR settings; neg_tol 0 keeps the library's default (LBM_EUNSTABLE
+    below -0.1 max(1, c_in)), < 0 turns the negative-concentration test
+    off."""
     taus = list(tau) if hasattr(tau, "__len__") else [tau] * nspecies
     taus = (taus + [1.0] * 3)[:3]
     cin = (list(c_in) + [0.0] * 3)[:3]
     return lbm_adr_params(nspecies, precision, (ctypes.c_double * 3)(*taus),
                           (ctypes.c_double * 3)(*cin), int(max_steps), tol,
-                          int(check_every), x_plane, flags)
+                          int(check_every), x_plane, flags, float(neg_tol))
 
 
 class ADRSolver:
@@ -455,6 +507,19 @@ class Batch:
                                      ctypes.byref(tile), ctypes.byref(grid)))
         return tile.value, grid.value
 
+    def conc(self, index: int, stream=None):
+        """lbm_batch_conc: concentrations [nspecies, ny, nx_pad] of lattice
+        ``index`` at its last checked step (its final state after solve)."""
+        import torch
+        g = self.geoms[index]
+        prec = self._p[0].precision
+        c = torch.empty((self._p[0].nspecies, g.ny, g.nx_pad),
+                        dtype=_field_dtype(prec), device=self.ws.device)
+        _check(load().lbm_batch_conc(self.handle, int(index),
+                                     ctypes.c_void_p(c.data_ptr()),
+                                     _stream_ptr(stream)))
+        return c
+
     def tuning(self):
         tile, grid = ctypes.c_int32(), ctypes.c_int32()
         ms = (ctypes.c_float * 8)()
@@ -477,6 +542,86 @@ class Batch:
     def close(self):
         if self.handle:
             load().lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# random walk particle tracking
+# ---------------------------------------------------------------------------
+class RWPT:
+    """lbm_rwpt_create / init / run over a torch workspace: particles in an
+    nx x ny channel with the fibers of a 6-column table, rates k1, k2 per
+    unit time, the device velocity u ([2, ny, nx_pad] float64, or None)."""
+
+    def __init__(self, nx: int, ny: int, fibers, k1: float, k2: float,
+                 u=None, D: float = 0.1, dt: float = 0.5,
+                 delta: float = 0.2, density: float = 10.0,
+                 radius_offset: float = 0.5, seed: int = 0,
+                 nspecies: int = 2, flags: int = 0, capacity: int = 1 << 20,
+                 device="cuda"):
+        lib = load()
+        fib = np.ascontiguousarray(np.asarray(fibers, dtype=np.float64)
+                                   .reshape(-1, 6))
+        self._fib = fib
+        self.params = lbm_rwpt_params(D, dt, delta, density, radius_offset,
+                                      int(seed), int(nspecies), int(flags))
+        self.u = u
+        self.capacity = int(capacity)
+        self.ws = _device_bytes(lib.lbm_rwpt_ws_bytes(self.capacity,
+                                                      fib.shape[0]), device)
+        h = ctypes.c_void_p()
+        _check(lib.lbm_rwpt_create(
+            nx, ny, fib.ctypes.data_as(_P), fib.shape[0], k1, k2,
+            ctypes.byref(self.params),
+            ctypes.c_void_p(u.data_ptr()) if u is not None else None,
+            self.capacity, ctypes.c_void_p(self.ws.data_ptr()),
+            self.ws.numel(), ctypes.byref(h)))
+        self.handle = h
+
+    def init(self, stream=None):
+        _check(load().lbm_rwpt_init(self.handle, _stream_ptr(stream)))
+        return self
+
+    def run(self, nsteps: int, stream=None, report: bool = True):
+        if not report:
+            _check(load().lbm_rwpt_run(self.handle, int(nsteps),
+                                       _stream_ptr(stream), None))
+            return None
+        info = lbm_rwpt_info()
+        _check(load().lbm_rwpt_run(self.handle, int(nsteps),
+                                   _stream_ptr(stream), ctypes.byref(info)))
+        return info.as_dict()
+
+    def reset_counts(self, stream=None):
+        _check(load().lbm_rwpt_reset_counts(self.handle,
+                                            _stream_ptr(stream)))
+        return self
+
+    def particles(self, stream=None):
+        """Host copies (x, y, species, id), sorted by id."""
+        n = self.capacity
+        x = np.empty(n)
+        y = np.empty(n)
+        s = np.empty(n, np.int32)
+        ids = np.empty(n, np.uint64)
+        cnt = ctypes.c_int64()
+        _check(load().lbm_rwpt_particles(
+            self.handle, _stream_ptr(stream), n, ctypes.byref(cnt),
+            x.ctypes.data_as(_P), y.ctypes.data_as(_P), s.ctypes.data_as(_P),
+            ids.ctypes.data_as(_P)))
+        m = cnt.value
+        o = np.argsort(ids[:m], kind="stable")
+        return x[:m][o], y[:m][o], s[:m][o], ids[:m][o]
+
+    def close(self):
+        if self.handle:
+            load().lbm_rwpt_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -176,6 +176,38 @@ def run(items=None, flows=None, precision: int = lbm.LBM_F32,
     return rows, shapes
 
 
+# ---------------------------------------------------------------------------
+# pure-diffusion cascade (Sec. IV.B, Figs. noflow and noflow_k001)
+# ---------------------------------------------------------------------------
+def noflow_cascade(kind: str, da: float, steps: int = 200000,
+                   every: int = 1000, precision: int = lbm.LBM_F64,
+                   n: int = 300, device="cuda"):
+    """Total amounts of A, B and C over time in the periodic box of
+    inputs.noflow_box (start: C_A = 1 on every fluid node, u = 0), each as a
+    fraction of the fluid nodes.  Returns a dict with the time points, the
+    three curves and the workload."""
+    import torch
+    w = inputs.noflow_box(kind, da, n=n)
+    g = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2)
+    g.set_periodic(lbm.LBM_PERIODIC_X | lbm.LBM_PERIODIC_Y).upload(device)
+    fluid = w.nx * w.ny - g.n_solid
+    dtype = torch.float64 if precision == lbm.LBM_F64 else torch.float32
+    u = torch.zeros((2, w.ny, g.nx_pad), dtype=dtype, device=g.ws.device)
+    prm = lbm.adr_params(3, w.tau_c, (0.0, 0.0, 0.0), precision=precision)
+    sv = lbm.ADRSolver(g, prm, u).init()
+    t, curves = [], [[], [], []]
+    done = 0
+    while done < steps:
+        info = sv.run(every)
+        done += every
+        t.append(done)
+        for s in range(3):
+            curves[s].append(info["mass"][s] / fluid)
+    sv.close()
+    return {"t": t, "A": curves[0], "B": curves[1], "C": curves[2],
+            "workload": w, "k1": w.k1, "k2": w.k2, "tau_c": w.tau_c}
+
+
 def as_table(rows) -> np.ndarray:
     """(geometry index, Pe, Da, eps) as an array, for plotting."""
     keys = sorted({r["geometry"] for r in rows})

@@ -156,3 +156,26 @@ def test_set_rates_rebuilds_links_and_validates(lib):
     g.set_rates(np.zeros(solid.shape), np.zeros(solid.shape))
     _, a4, b4 = g.fields()
     assert not a4.any() and not b4.any()
+
+
+def test_set_periodic_status_and_stale_upload(lib):
+    """lbm_geometry_set_periodic: unknown flags are refused; setting the
+    flags rebuilds the link words and leaves the device copy stale, so a
+    solver cannot be created before the next upload."""
+    g = lbm.Geometry(16, 8, np.array([[8.0, 4.0, 2.0, 1, 0, -1]]), 0.1, 0.0)
+    assert lib.lbm_geometry_set_periodic(g.handle, 4) == lbm.LBM_EINVAL
+    assert lib.lbm_geometry_set_periodic(None, 1) == lbm.LBM_EINVAL
+    for flags in (lbm.LBM_PERIODIC_X, lbm.LBM_PERIODIC_Y,
+                  lbm.LBM_PERIODIC_X | lbm.LBM_PERIODIC_Y, 0):
+        assert lib.lbm_geometry_set_periodic(g.handle, flags) == lbm.LBM_OK
+    prm = lbm.adr_params(3, 0.8)
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(256)
+    st = lib.lbm_adr_create(g.handle, ctypes.byref(prm), fake, fake, 1 << 20,
+                            ctypes.byref(h))
+    assert st == lbm.LBM_EINVAL
+    assert b"not uploaded" in lib.lbm_last_error()
+    # the raster itself does not change
+    s, a, _ = g.fields()
+    so, ao, _ = oracle.raster(16, 8, [[8.0, 4.0, 2.0, 1, 0, -1]], 0.1, 0.0)
+    assert np.array_equal(s, so) and np.array_equal(a, ao)

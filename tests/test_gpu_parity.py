@@ -328,6 +328,31 @@ def cascade_oracle():
     return w, ux, uy, ref, nflow, nadr, xp
 
 
+def test_cascade_full_lattice_pe100_f64(cascade_oracle):
+    """The same lattice at Pe = 100, where tau_c = 0.512 comes close to the
+    1/2 stability limit (Appendix C warns of negative populations there):
+    FP64 matches the oracle at 2000 steps, and the most negative
+    concentration the check steps report equals the oracle's (B undershoots
+    a little behind the catalytic fibers; it is reported, not an error)."""
+    w0, ux, uy, _, nflow, nadr, xp = cascade_oracle
+    w = inputs.two_membrane_cascade(seed=0, pe=100.0)
+    assert abs(w.tau_c - 0.512) < 1e-12
+    solid, kab, kbc = oracle.raster(w.nx, w.ny, w.fibers, w.k1, w.k2)
+    prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, [w.tau_c] * 3,
+                             [1, 0, 0])
+    ref = prob.run(nadr, xp=xp)
+    cmin = np.minimum(ref["conc"].min(axis=(1, 2)), 0.0)
+    geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
+    u = _dev_u(ux, uy, geom.nx_pad, torch.float64)
+    conc, info = _run_gpu_adr(geom, u, 3, [w.tau_c] * 3, [1, 0, 0],
+                              lbm.LBM_F64, nadr, xp=xp)
+    rel = np.linalg.norm(conc - ref["conc"]) / np.linalg.norm(ref["conc"])
+    assert rel < 1e-10
+    assert np.allclose(info["flux"], ref["flux"], rtol=1e-10, atol=1e-15)
+    assert ref["conc"][1].max() > 1e-4       # B is made at the membrane
+    assert np.allclose(info["c_min"], cmin, rtol=1e-8, atol=1e-14)
+
+
 def test_cascade_full_lattice_f64(cascade_oracle):
     w, ux, uy, ref, nflow, nadr, xp = cascade_oracle
     geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()

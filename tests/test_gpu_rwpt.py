@@ -1,0 +1,105 @@
+"""Random walk particle tracking (Sec. III.B) on the GPU (lbm_rwpt_*)
+against the CPU particle oracle: every particle's id, species and position
+equal bit for bit after the same steps (both sides draw from the same
+counter-based SplitMix64 streams and round every operation once), and the
+outlet counts equal exactly.  The velocity field is the oracle's own flow."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from oracle import rwpt as orwpt  # noqa: E402
+from paper_2109_04455_gb300 import lbm  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2109_04455_gb300 import _build
+    _build.build()
+    oracle.build()
+    lbm.load()
+
+
+NX, NY = 61, 26
+FIBERS = np.array([[18.3, 12.6, 4.0, 1, 0, -1],
+                   [34.7, 9.1, 3.0, 2, 0, -1],
+                   [45.2, 17.4, 3.5, 3, 2.3, -1],
+                   [28.0, 21.0, 2.0, 1, 0, 0.3]])
+
+
+@pytest.fixture(scope="module")
+def flow():
+    solid, _, _ = oracle.raster(NX, NY, FIBERS, 0.0, 0.0)
+    _, ux, uy, _ = oracle.flow_run(solid, 0.8, 0.05, 1500)
+    pad = (NX + 31) // 32 * 32
+    u = torch.zeros((2, NY, pad), dtype=torch.float64)
+    u[0, :, :NX] = torch.from_numpy(ux)
+    u[1, :, :NX] = torch.from_numpy(uy)
+    return ux, uy, u.cuda()
+
+
+def _same(gpu, ref):
+    gx, gy, gs, gid = gpu.particles()
+    rx, ry, rs, rid = ref.p.sorted()
+    assert np.array_equal(gid, rid)
+    assert np.array_equal(gs, rs)
+    assert np.array_equal(gx, rx) and np.array_equal(gy, ry)
+    return len(gid)
+
+
+@pytest.mark.parametrize("ns", [2, 3])
+def test_rwpt_channel_bit_for_bit(flow, ns):
+    ux, uy, u = flow
+    k1, k2 = 0.3, 0.5
+    kw = dict(D=0.04, dt=0.5, delta=0.2, density=4.0, radius_offset=0.5,
+              seed=2024 + ns, nspecies=ns)
+    g = lbm.RWPT(NX, NY, FIBERS, k1, k2, u, capacity=1 << 16, **kw).init()
+    r = orwpt.RWPT(NX, NY, FIBERS, k1, k2, (ux, uy), **kw).init()
+    assert _same(g, r) > 4000
+    for n in (1, 9, 290):
+        info = g.run(n)
+        r.run(n)
+        _same(g, r)
+        assert info["out"] == [int(v) for v in r.out]
+        assert not info["overflow"]
+    assert r.out[0] > 0 and r.out[1] > 0
+    if ns == 3:
+        assert (r.p.s == 2).any()
+    # a new counting window
+    g.reset_counts()
+    r.out[:] = 0
+    info = g.run(50)
+    r.run(50)
+    assert info["out"] == [int(v) for v in r.out]
+    assert info["window_steps"] == 50 and info["steps"] == 350
+
+
+def test_rwpt_periodic_homogeneous_bit_for_bit():
+    kw = dict(D=0.2, dt=0.5, delta=0.2, density=3.0, radius_offset=0.0,
+              seed=7, nspecies=3)
+    fib = np.array([[10.0, 10.0, 3.0, 0, 0, -1]])      # inert obstacle
+    g = lbm.RWPT(40, 30, fib, 0.2, 0.1, None, capacity=1 << 14,
+                 flags=lbm.LBM_RWPT_PERIODIC | lbm.LBM_RWPT_HOMOGENEOUS,
+                 **kw).init()
+    r = orwpt.RWPT(40, 30, fib, 0.2, 0.1, None, periodic=True,
+                   homogeneous=True, **kw).init()
+    for n in (1, 20, 80):
+        info = g.run(n)
+        r.run(n)
+        _same(g, r)
+    assert info["alive"] == len(r.p.id) and info["out"] == [0, 0, 0]
+    assert (r.p.s == 1).any() and (r.p.s == 2).any()
+
+
+def test_rwpt_capacity_overflow_is_reported(flow):
+    _, _, u = flow
+    g = lbm.RWPT(NX, NY, FIBERS, 0.1, 0.1, u, D=0.04, density=4.0,
+                 capacity=1000).init()
+    with pytest.raises(lbm.LBMError) as e:
+        g.run(2)
+    assert e.value.status == lbm.LBM_ENOMEM

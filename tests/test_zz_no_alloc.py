@@ -23,8 +23,7 @@ def _built():
     lbm.load()
 
 
-def _solver(prec):
-    nx, ny = 261, 37
+def _solver(prec, nx=261, ny=37):
     rng = inputs.SplitMix64(11)
     rows = inputs.place_fibers(rng, 40, 120, ny, 5, 3, 5, 2.0,
                                lambda r: (1, 0.0))
@@ -46,6 +45,18 @@ def test_outflux_noalloc_matches_regular_path(prec):
         info = sv.run(nsteps)
         got = lbm.lbm_adr_outflux_noalloc(sv, x_plane=PLANE)
         # same double sums of the same stored values, in another order
+        assert np.allclose(got, info["flux"], rtol=1e-12, atol=1e-15)
+    assert abs(got[0]) > 0 and abs(got[1]) > 0
+
+
+@pytest.mark.parametrize("prec", [lbm.LBM_F64, lbm.LBM_F32, lbm.LBM_F16DEV])
+def test_outflux_noalloc_many_row_blocks(prec):
+    """ny = 600 spans three 256-row blocks of the partial kernel, so the
+    final kernel folds several block partials before dividing by ny."""
+    geom, sv = _solver(prec, nx=261, ny=600)
+    for nsteps in (300, 200):
+        info = sv.run(nsteps)
+        got = lbm.lbm_adr_outflux_noalloc(sv, x_plane=PLANE)
         assert np.allclose(got, info["flux"], rtol=1e-12, atol=1e-15)
     assert abs(got[0]) > 0 and abs(got[1]) > 0
 
