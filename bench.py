@@ -8,7 +8,16 @@ Pe = 50, Da = 0.5, species A, B, C.  Set-up (untimed): raster, upload, flow
 three species, the last two of which also record the concentration change,
 followed by the outflux reduction and the efficiency read back to the host:
 one pass of the whole hot path.  The population state (14.5 GB in FP32) is
-far larger than L2, so no flush is needed between steps.
+far larger than L2, so no flush is needed between steps.  The flow is solved
+once in FP64 and cast to float for the float precisions.
+
+The line is the --precision run (FP32 by default).  On one GPU it also
+carries, unless --no-extra: the other two precisions timed the same way
+(fewer steps; their own roofline and clocks; the FP64 step's roofline is
+its FP64 arithmetic against the FMA rate measured on the same GPU by
+lbm_fp64_fma_tflops), and an efficiency check at equal step counts: FP32
+and FP16 storage against FP64 on the full lattice, outfluxes on a plane
+64 nodes behind the first (A->B) membrane.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f16dev|f64]
 python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
@@ -50,9 +59,16 @@ def _args():
     ap.add_argument("--ny", type=int, default=4096)
     ap.add_argument("--fibers-per-band", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave out the other precisions' records and the "
+                         "equal-step efficiency check")
+    ap.add_argument("--extra-steps", type=int, default=5,
+                    help="timed bench steps of each other precision")
+    ap.add_argument("--eps-steps", type=int, default=3000,
+                    help="ADR steps of the equal-step efficiency check")
     ap.add_argument("--workload", default="large",
                     choices=["large", "sweep", "adjoint", "series",
-                             "cascade"],
+                             "cascade", "noflow", "adjoint-check"],
                     help="large: the 67M-node membrane (default line); "
                          "sweep: the 64-instance Pe x Da sweep, batched "
                          "FP32 / FP16 against unbatched FP64 (solves/s); "
@@ -63,7 +79,9 @@ def _args():
                          "batched, to steady state; cascade: the "
                          "two-membrane cascade (2048x512) at Da = 1 and "
                          "Pe = 1, 10, 100 to steady state in FP64 and "
-                         "FP32")
+                         "FP32; noflow: the pure-diffusion cascade of "
+                         "Sec. IV.B (periodic 300x300 box, fiber pair and "
+                         "side-by-side fiber, Da = 150 and 1.5)")
     ap.add_argument("--adjoint-iters", type=int, default=200)
     ap.add_argument("--sweep-instances", type=int, default=64)
     ap.add_argument("--sweep-max-steps", type=int, default=5000)
@@ -72,6 +90,9 @@ def _args():
                          "runs every instance exactly --sweep-max-steps "
                          "steps in every precision")
     ap.add_argument("--sweep-flow-steps", type=int, default=3000)
+    ap.add_argument("--fd-steps", type=int, default=150000,
+                    help="adjoint-check: steps of each perturbed solve "
+                         "after the base state")
     ap.add_argument("--cascade-pe", default="1,10,100")
     ap.add_argument("--cascade-max-steps", type=int, default=3000000)
     return ap.parse_args()
@@ -150,10 +171,6 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
-# FP64 arithmetic peak of the part: 2 double FMA instructions per clock per
-# SM (ncu: the FP64 pipe of the FP64 step was 86% busy at 1.71 double
-# instructions per SM clock) x 152 SMs x 2.07 GHz x 2 flops per FMA
-FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 # algorithmic double flops of one FP64 interior node update with the E table:
 # per species 8 additions for C and, per population, C E_i - g and
 # g + omega (...) as two FMAs (4 flops)
@@ -337,6 +354,135 @@ def run_reference(a):
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
+def _gpu_index(dev):
+    gpu_index = dev.index
+    try:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            gpu_index = int(vis.split(",")[dev.index])
+    except ValueError:
+        pass
+    return gpu_index
+
+
+def _measure(precision, geom, w, u, steps, warmup, dev, world, fp64_peak):
+    """Time `steps` bench steps (CHUNK ADR steps each, the last two checked,
+    then the outflux and the efficiency read back) of one precision after
+    `warmup` untimed ones.  Returns the record (throughput, the roofline of
+    the step kernel, clocks, launches) and the solver."""
+    import torch
+
+    from paper_2109_04455_gb300 import lbm
+    prec = lbm.PRECISIONS[precision]
+    prm = lbm.adr_params(SPECIES, w.tau_c, w.c_in, precision=prec)
+    solver = lbm.ADRSolver(geom, prm, u).init()
+    stream = torch.cuda.current_stream()
+
+    def bench_step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        solver.run(CHUNK - 2, check=False)
+        if evs is not None:
+            evs[1].record(stream)
+        return solver.run(2)
+
+    info = None
+    for _ in range(warmup):
+        info = bench_step()
+    ev_plain = [(torch.cuda.Event(enable_timing=True),
+                 torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+        enable_timing=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(_gpu_index(dev)) as clk:
+        t0.record(stream)
+        for k in range(steps):
+            info = bench_step(ev_plain[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    elapsed = max_over_ranks(t0.elapsed_time(t1) * 1e-3, dev)
+    plain_s = sum(e0.elapsed_time(e1) for e0, e1 in ev_plain) * 1e-3
+    # per ADR step the bulk kernel and (when the lattice has boundary nodes)
+    # the boundary-node kernel; per bench step the two-level partial-sum
+    # reduce (2 launches) and the outflux kernel
+    lw = geom.ws[:4 * geom.nx_pad * geom.ny].view(torch.int32).cpu().numpy()
+    has_bnd = bool(((lw != 0) & (lw != -1)).any())
+    launches_per_step = CHUNK * (2 if has_bnd else 1) + 3
+    updates = SPECIES * w.nx * w.ny * CHUNK * steps
+    value = job_throughput(updates, world, elapsed)
+    alg_bytes, n_fluid, per_fluid = _algorithmic_bytes(geom, w, precision)
+    step_launch_s = plain_s / ((CHUNK - 2) * steps)
+    achieved = alg_bytes / step_launch_s / 1e9
+    peak, peak_kind = _peak_hbm()
+    traffic = _ncu_traffic(precision, n_fluid)
+    kernel = ("adr_bulk_pair_kernel<3 species,step> (f16dev)"
+              if precision == "f16dev" else
+              f"adr_bulk_kernel<{precision},3 species,step>")
+    if precision != "f64":
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": f"{peak_kind} (copy bandwidth)"}
+    else:
+        tf = FP64_FLOPS_PER_NODE * n_fluid / step_launch_s / 1e12
+        roof = {"bound": "alu", "achieved": tf, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": tf / fp64_peak,
+                "peak_kind": "measured: lbm_fp64_fma_tflops (independent "
+                             "FP64 FMA chains on this GPU, this run)",
+                "hbm_gbs": achieved, "hbm_frac": achieved / peak}
+    roof.update({"traffic": traffic, "kernel": kernel,
+                 "algorithmic_bytes_per_launch": alg_bytes,
+                 "bytes_per_fluid_node": per_fluid, "fluid_nodes": n_fluid,
+                 "avg_launch_ms": step_launch_s * 1e3})
+    rec = {"value": value, "unit": UNIT, "steps": steps, "warmup": warmup,
+           "ms_per_step": elapsed / steps * 1e3,
+           "dtype": {"f32": "f32", "f16dev": "f16-storage/f32-compute",
+                     "f64": "f64"}[precision],
+           "roofline": roof, "clocks": clk.summary(),
+           "gpu_launches": launches_per_step * steps,
+           "eps": info["eps"], "adr_residual": info["residual"]}
+    return rec, solver, bench_step
+
+
+def _eps_check(geom, w, u64, steps, plane, dev):
+    """FP32 and FP16 storage against FP64 on the full lattice at equal step
+    counts from the same start on the same FP64 flow: outfluxes on a plane
+    behind the first (A->B) membrane, where B made there crosses.  Reports
+    each precision's fluxes, the A->B efficiency N_B / (N_A + N_B) on that
+    plane, the cascade efficiency of Eq. (A-B) (N_C / sum N) and the
+    differences to FP64."""
+    import torch
+
+    from paper_2109_04455_gb300 import lbm
+    out = {"plane": plane, "steps": steps,
+           "flow": "FP64 (cast to float for FP32 / FP16)"}
+    ref = None
+    for name in ("f64", "f32", "f16dev"):
+        prec = lbm.PRECISIONS[name]
+        prm = lbm.adr_params(SPECIES, w.tau_c, w.c_in, precision=prec,
+                             max_steps=steps, x_plane=plane)
+        _, info = lbm.lbm_adr_solve(geom, prm, u64 if name == "f64"
+                                    else u64.float(), want_conc=False)
+        torch.cuda.empty_cache()
+        f = info["flux"]
+        rec = {"flux": f, "eps_ab": f[1] / (f[0] + f[1]),
+               "eps": info["eps"], "c_min": info["c_min"]}
+        if ref is None:
+            ref = rec
+        else:
+            rec["eps_ab_err_vs_f64"] = abs(rec["eps_ab"] - ref["eps_ab"])
+            rec["eps_err_vs_f64"] = abs(rec["eps"] - ref["eps"])
+            rec["flux_rel_err_vs_f64"] = max(
+                abs(a - b) / abs(ref["flux"][0]) for a, b in zip(f, ref["flux"]))
+        out[name] = rec
+    return out
+
+
 def run_gpu(a):
     import torch
     import torch.distributed as dist
@@ -352,88 +498,38 @@ def run_gpu(a):
     else:
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-    prec = lbm.PRECISIONS[a.precision]
     w = _workload(a, seed=rank)
 
-    # ---- set-up (untimed): raster, upload, flow
+    # ---- set-up (untimed): raster, upload, flow (FP64: one velocity field
+    # for every precision, cast to float for the float paths)
     geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload(dev)
     stream = torch.cuda.current_stream()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
         enable_timing=True)
     f0.record(stream)
-    u, finfo = lbm.lbm_flow_solve(geom, w.tau_flow, w.u0, a.flow_steps,
-                                  precision=lbm.LBM_F64 if prec == lbm.LBM_F64
-                                  else lbm.LBM_F32)
+    u64, finfo = lbm.lbm_flow_solve(geom, w.tau_flow, w.u0, a.flow_steps,
+                                    precision=lbm.LBM_F64)
     f1.record(stream)
     torch.cuda.synchronize()
     flow_ms = f0.elapsed_time(f1)
     flow_mlups = w.nx * w.ny * a.flow_steps / (flow_ms * 1e-3) / 1e6
+    fp64_peak = lbm.lbm_fp64_fma_tflops()
 
-    prm = lbm.adr_params(SPECIES, w.tau_c, w.c_in, precision=prec)
-    solver = lbm.ADRSolver(geom, prm, u).init()
+    def vel(precision):
+        return u64 if precision == "f64" else u64.float()
 
-    def bench_step(evs=None):
-        if evs is not None:
-            evs[0].record(stream)
-        solver.run(CHUNK - 2, check=False)
-        if evs is not None:
-            evs[1].record(stream)
-        return solver.run(2)
-
-    for _ in range(a.warmup):
-        info = bench_step()
-
-    # ---- timed region
-    n_ev = a.steps
-    ev_plain = [(torch.cuda.Event(enable_timing=True),
-                 torch.cuda.Event(enable_timing=True)) for _ in range(n_ev)]
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
-        enable_timing=True)
-    gpu_index = dev.index
-    try:
-        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-        if vis:
-            gpu_index = int(vis.split(",")[dev.index])
-    except ValueError:
-        pass
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(gpu_index) as clk:
-        t0.record(stream)
-        for k in range(a.steps):
-            info = bench_step(ev_plain[k])
-        t1.record(stream)
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    elapsed = t0.elapsed_time(t1) * 1e-3
-    plain_s = sum(e0.elapsed_time(e1) for e0, e1 in ev_plain) * 1e-3
-    # per ADR step the bulk kernel and (when the lattice has boundary nodes)
-    # the boundary-node kernel; per bench step the two-level partial-sum
-    # reduce (2 launches) and the outflux kernel
-    import numpy as np
-    lw = geom.ws[:4 * geom.nx_pad * geom.ny].view(torch.int32).cpu().numpy()
-    has_bnd = bool(((lw != 0) & (lw != -1)).any())
-    launches_per_step = CHUNK * (2 if has_bnd else 1) + 3
-    elapsed = max_over_ranks(elapsed, dev)
-    updates = SPECIES * w.nx * w.ny * CHUNK * a.steps
-    value = job_throughput(updates, world, elapsed)
-
-    # roofline of the dominant kernel (the fused ADR step)
-    alg_bytes, n_fluid, per_fluid = _algorithmic_bytes(geom, w, a.precision)
-    step_launch_s = plain_s / ((CHUNK - 2) * a.steps)
-    achieved = alg_bytes / step_launch_s / 1e9
-    peak, peak_kind = _peak_hbm()
-    traffic = _ncu_traffic(a.precision, n_fluid)
+    main, solver, bench_step = _measure(a.precision, geom, w,
+                                        vel(a.precision), a.steps, a.warmup,
+                                        dev, world, fp64_peak)
 
     # ---- end to end through the public API with host buffers
+    u = solver.u
     ws_host = torch.empty(geom.ws.numel(), dtype=torch.uint8, pin_memory=True)
     ws_host.copy_(geom.ws)
     u_host = torch.empty(u.shape, dtype=u.dtype, pin_memory=True)
     u_host.copy_(u)
     h2d = ws_host.numel() + u_host.numel() * u_host.element_size()
-    d2h = 16 * 8
+    d2h = 24 * 8
     e2e_steps = max(1, a.e2e_steps)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
@@ -445,51 +541,52 @@ def run_gpu(a):
         bench_step()          # ends with the D2H read of flux / eps
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) * 1e-3
-    e2e_s = max_over_ranks(e2e_s, dev)
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) * 1e-3, dev)
     e2e_value = job_throughput(SPECIES * w.nx * w.ny * CHUNK * e2e_steps,
                                world, e2e_s)
+    solver.close()
+    del solver, bench_step
+    torch.cuda.empty_cache()
+
+    # ---- the other precisions (timed the same way, fewer steps) and the
+    # efficiency check at equal step counts (one GPU only)
+    others, eps_check = {}, None
+    if world == 1 and not a.no_extra:
+        for name in ("f32", "f16dev", "f64"):
+            if name == a.precision:
+                continue
+            rec, sv, _ = _measure(name, geom, w, vel(name), a.extra_steps, 3,
+                                  dev, world, fp64_peak)
+            sv.close()
+            del sv
+            torch.cuda.empty_cache()
+            others[name] = rec
+        plane = int(round(2 * w.nx / 9.0)) + 64
+        eps_check = _eps_check(geom, w, u64, a.eps_steps, plane, dev)
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": a.steps, "warmup": a.warmup,
-            "ms_per_step": elapsed / a.steps * 1e3,
+            "metric": METRIC, "value": main["value"], "unit": UNIT,
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": main["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"f32": "f32", "f16dev": "f16-storage/f32-compute",
-                      "f64": "f64"}[a.precision],
+            "dtype": main["dtype"],
             "data": "synthetic (seeded fiber geometry)",
             "config": _config(a, w),
-            "roofline": ({"bound": "hbm", "achieved": achieved,
-                          "peak": peak, "unit": "GB/s",
-                          "frac": achieved / peak,
-                          "peak_kind": f"{peak_kind} (copy bandwidth)"}
-                         if a.precision != "f64" else
-                         {"bound": "alu",
-                          "achieved": FP64_FLOPS_PER_NODE * n_fluid /
-                          step_launch_s / 1e12,
-                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                          "frac": FP64_FLOPS_PER_NODE * n_fluid /
-                          step_launch_s / 1e12 / FP64_PEAK_TFLOPS,
-                          "peak_kind": "derived: 2 FP64 FMA/clk/SM x 152 "
-                                       "SMs x 2.07 GHz",
-                          "hbm_gbs": achieved}) | {
-                         "traffic": traffic,
-                         "kernel": ("adr_bulk_pair_kernel<3 species,step> "
-                                    "(f16dev)" if a.precision == "f16dev" else
-                                    f"adr_bulk_kernel<{a.precision},3 species,step>"),
-                         "algorithmic_bytes_per_launch": alg_bytes,
-                         "bytes_per_fluid_node": per_fluid,
-                         "fluid_nodes": n_fluid,
-                         "avg_launch_ms": step_launch_s * 1e3},
+            "roofline": main["roofline"],
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches_per_step * a.steps,
-            "clocks": clk.summary(),
+            "gpu_launches": main["gpu_launches"],
+            "clocks": main["clocks"],
             "flow": {"mlups": flow_mlups, "steps": a.flow_steps,
-                     "residual": finfo["residual"]},
-            "eps": info["eps"], "adr_residual": info["residual"],
+                     "precision": "f64", "residual": finfo["residual"]},
+            "eps": main["eps"], "adr_residual": main["adr_residual"],
+            "fp64_fma_tflops_measured": fp64_peak,
         }
+        if others:
+            line["other_precisions"] = others
+        if eps_check:
+            line["eps_check"] = eps_check
         if not a.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
@@ -623,7 +720,14 @@ def run_adjoint(a):
     u, _ = lbm.lbm_flow_solve(geom, w.tau_flow, w.u0, a.flow_steps,
                               precision=lbm.LBM_F64 if prec == lbm.LBM_F64
                               else lbm.LBM_F32)
-    prm = lbm.adr_params(SPECIES, w.tau_c, w.c_in, precision=prec)
+    # flux plane 8 nodes behind the first (A->B) membrane: the adjoint
+    # starts there and runs upstream at the flow speed, so within the timed
+    # iterations it reaches that membrane's last fibers and the gradient is
+    # not zero (at the outlet, 1800 nodes behind the last membrane, it would
+    # need ~55000 iterations)
+    plane = int(round(2 * w.nx / 9.0)) + 8
+    prm = lbm.adr_params(SPECIES, w.tau_c, w.c_in, precision=prec,
+                         x_plane=plane)
     sv = lbm.ADRSolver(geom, prm, u).init()
     sv.run(CHUNK - 2, check=False)
     sv.run(2)
@@ -671,8 +775,10 @@ def run_adjoint(a):
                          "bytes_per_fluid_node": per_fluid,
                          "avg_iteration_ms": per_it * 1e3},
             "clocks": clk.summary(),
-            "eps": info["eps"],
-            "dw_abs_max": float(dw.abs().max().item())}
+            "eps": info["eps"], "flux_plane": plane,
+            "flux": info["flux"],
+            "dw_abs_max": float(dw.abs().max().item()),
+            "dw_nonzero_fibers": int((dw != 0).sum().item())}
     print(json.dumps(line), flush=True)
 
 
@@ -703,6 +809,18 @@ def run_series(a):
                               max_steps=300000)
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
+    # efficiency against Da at Pe = 1, 7, 20 (Fig. singleAB_Da), and at
+    # Pe = 7 with the node-wise reaction as well (Fig. node_vs_pop)
+    da_items = series.da_workloads()
+    da_rows, _ = series.run(da_items, flows, precision=prec, tol=2e-7,
+                            max_steps=300000)
+    pe7 = [it for it in da_items if it[1].pe == 7.0]
+    nw_rows, _ = series.run(pe7, flows, precision=prec, tol=2e-7,
+                            max_steps=300000, flags=lbm.LBM_ADR_NODEWISE)
+    for r in da_rows:
+        r["series"] = "eps_vs_da"
+    for r in nw_rows:
+        r["series"] = "eps_vs_da_nodewise"
     out = {"metric": "paper 2D series solves/s (ADR to steady state)",
            "value": len(rows) / t, "unit": "solves/s",
            "higher_is_better": True, "seconds": t, "dtype": a.precision,
@@ -713,7 +831,8 @@ def run_series(a):
            "launch_shapes": shapes,
            "timing": "host clock around the batched solves, tuning included",
            "rows": [{k: (round(v, 8) if isinstance(v, float) else v)
-                     for k, v in r.items() if k != "flux"} for r in rows]}
+                     for k, v in r.items() if k != "flux"}
+                    for r in rows + da_rows + nw_rows]}
     print(json.dumps(out), flush=True)
 
 
@@ -797,6 +916,124 @@ def run_cascade(a):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# the pure-diffusion cascade (Sec. IV.B)
+# ---------------------------------------------------------------------------
+def run_noflow(a, steps=200000, every=1000):
+    """Totals of A, B and C over time in the periodic 300 x 300 box without
+    flow (Figs. noflow, noflow_k001): the A->B / B->C fiber pair (R = 5,
+    surfaces 100 apart) and the side-by-side fiber (R = 10), Da = 150 and
+    1.5, FP64.  Reports the curves at a few times and the time at which
+    half of the initial A has become C."""
+    import torch
+
+    from paper_2109_04455_gb300 import lbm, series
+    torch.cuda.set_device(0)
+    rows = []
+    t_all = time.perf_counter()
+    for da in (150.0, 1.5):
+        for kind in ("pair", "side_by_side"):
+            t0 = time.perf_counter()
+            out = series.noflow_cascade(kind, da, steps=steps, every=every,
+                                        precision=lbm.LBM_F64)
+            dt = time.perf_counter() - t0
+            t = out["t"]
+            half = next((tt for tt, c in zip(t, out["C"]) if c >= 0.5), None)
+            pick = [i for i, tt in enumerate(t)
+                    if tt in (1000, 5000, 20000, 50000, 100000, 200000)]
+            rows.append({"kind": kind, "da": da, "k1": out["k1"],
+                         "k2": out["k2"], "tau": out["tau_c"], "seconds": dt,
+                         "t_half_C": half,
+                         "curve": {str(t[i]): [round(out["A"][i], 6),
+                                               round(out["B"][i], 6),
+                                               round(out["C"][i], 6)]
+                                   for i in pick}})
+            print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"metric": "pure-diffusion cascade (periodic box)",
+                      "steps": steps, "seconds": time.perf_counter() - t_all,
+                      "rows": rows}), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the adjoint on the two-membrane cascade, fiber by fiber
+# ---------------------------------------------------------------------------
+def run_adjoint_check(a):
+    """The adjoint check of the two-membrane cascade lattice (2048 x 512,
+    80 fibers, seed 0, Pe = 10, Da1 = Da2 = 1, relaxed weights 0.9 on the
+    A->B fibers and 0.1 on the B->C fibers).  FP64: steady state to a
+    per-step residual of 1e-13 and the adjoint to 1e-13.  FP32 populations
+    (FP64 sums): steady state to 1e-7 and the adjoint at FP64's iteration
+    count.  Then for each of 16 random fibers the central difference with
+    h = 1e-4 of two FP64 solves warm-started from the base state, each run
+    a fixed --fd-steps steps (a solve stopped by the per-step residual
+    leaves ~1e-3 of so small a perturbation unrelaxed; 150000 steps leave
+    ~1e-5).  Reports per fiber the difference quotient, the FP64 and FP32
+    adjoint values and their relative differences."""
+    import numpy as np
+    import torch
+
+    from paper_2109_04455_gb300 import inputs, lbm
+    torch.cuda.set_device(0)
+    t_all = time.perf_counter()
+    w = inputs.two_membrane_cascade(seed=0, pe=10.0)
+    fib = w.fibers.copy()
+    fib[:, 5] = np.where(fib[:, 3] == 1, 0.9, 0.1)
+    nf = fib.shape[0]
+    g0 = lbm.Geometry(w.nx, w.ny, fib, w.k1, w.k2).upload()
+    u, _ = lbm.lbm_flow_solve(g0, w.tau_flow, w.u0, 400000, tol=1e-10,
+                              check_every=1000, precision=lbm.LBM_F64)
+
+    def solver(fb, prec, uu):
+        g = lbm.Geometry(w.nx, w.ny, fb, w.k1, w.k2).upload()
+        return g, lbm.ADRSolver(g, lbm.adr_params(3, w.tau_c,
+                                                  precision=prec), uu).init()
+
+    g, sv = solver(fib, lbm.LBM_F64, u)
+    base_info = sv.solve(1e-13, 1000, 2000000)
+    base = sv.state_save()
+    _, _, dw, ainfo = sv.adjoint(2000000, tol=1e-13, check_every=1000,
+                                 nfibers=nf)
+    dw = dw.cpu().numpy()
+    g32, sv32 = solver(fib, lbm.LBM_F32, u.float())
+    sv32.solve(1e-7, 1000, 2000000)
+    _, _, dw32, _ = sv32.adjoint(ainfo["steps"], tol=0.0,
+                                 check_every=ainfo["steps"], nfibers=nf)
+    dw32 = dw32.cpu().numpy()
+    rng = np.random.default_rng(4)
+    pick = rng.choice(nf, 16, replace=False)
+    h = 1e-4
+    rows = []
+    for f in pick:
+        e = []
+        for sgn in (1.0, -1.0):
+            fb = fib.copy()
+            fb[f, 5] += sgn * h
+            gg, sp = solver(fb, lbm.LBM_F64, u)
+            sp.state_load(base)
+            info = sp.run(a.fd_steps)
+            e.append(info["eps"])
+            sp.close()
+        fd = (e[0] - e[1]) / (2 * h)
+        rows.append({"fiber": int(f), "cat": int(fib[f, 3]), "fd": fd,
+                     "adjoint_f64": float(dw[f]), "adjoint_f32": float(dw32[f]),
+                     "rel_f64_vs_fd": (float(dw[f]) - fd) / fd,
+                     "rel_f32_vs_f64": (float(dw32[f]) - float(dw[f]))
+                     / float(dw[f])})
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({
+        "metric": "adjoint check, two-membrane cascade (2048x512, Pe 10, Da 1)",
+        "base": {"steps": base_info["steps"], "residual": base_info["residual"],
+                 "eps": base_info["eps"]},
+        "adjoint_f64": {"iterations": ainfo["steps"],
+                        "residual": ainfo["residual"]},
+        "f32_vs_f64_rel_l2": float(np.linalg.norm(dw32 - dw) /
+                                   np.linalg.norm(dw)),
+        "h": h, "fd_steps": a.fd_steps,
+        "max_rel_f64_vs_fd": max(abs(r["rel_f64_vs_fd"]) for r in rows),
+        "max_rel_f32_vs_f64": max(abs(r["rel_f32_vs_f64"]) for r in rows),
+        "seconds": time.perf_counter() - t_all, "rows": rows}), flush=True)
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -809,6 +1046,10 @@ def main():
         run_series(a)
     elif a.workload == "cascade":
         run_cascade(a)
+    elif a.workload == "noflow":
+        run_noflow(a)
+    elif a.workload == "adjoint-check":
+        run_adjoint_check(a)
     else:
         run_gpu(a)
 

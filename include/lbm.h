@@ -449,6 +449,13 @@ lbm_status lbm_rwpt_particles(lbm_rwpt *r, void *stream, int64_t max_count,
  * Host arithmetic only.  LBM_EINVAL for other nspecies or a zero sum. */
 lbm_status lbm_efficiency(const double *flux, int32_t nspecies, double *eps);
 
+/* Double-precision FMA throughput of the current device in TFLOP/s (2 flops
+ * per FMA), measured by a short kernel of independent FMA chains (best of
+ * three timed launches after a warm-up, a few ms in all; synchronises
+ * `stream`).  No counterpart in the paper: it is the measured denominator of
+ * the FP64 step's roofline, since that step is bound by the FP64 pipe. */
+lbm_status lbm_fp64_fma_tflops(void *stream, double *tflops);
+
 /* Outfluxes N_s on the plane x_plane (< 0 selects nx - 3) of the solver's
  * current state, written to flux_out (host, 3 doubles; 0 for absent
  * species), without any device workspace.  The paper has no counterpart:

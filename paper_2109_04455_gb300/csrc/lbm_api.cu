@@ -1141,3 +1141,69 @@ extern "C" lbm_status lbm_adr_outflux_noalloc(lbm_adr_solver *s,
   for (int k = 0; k < 3; ++k) flux_out[k] = k < ns ? h[k] : 0.0;
   return LBM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// FP64 FMA throughput of the device: the denominator of the FP64 step's
+// arithmetic roofline (that step is bound by the double-precision pipe, not
+// by HBM).  Sixteen independent FMA chains per thread keep the pipe busy
+// whatever its latency; the chains' sum is compared with a value it cannot
+// take, so that the compiler keeps every FMA.
+// ---------------------------------------------------------------------------
+namespace lbm {
+namespace peak {
+constexpr int kChains = 16;
+constexpr int kThreads = 256;
+static __device__ double g_sink;
+
+__global__ void __launch_bounds__(kThreads)
+    fp64_fma_kernel(int iters, double seed, double mul, double add) {
+  double x[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) x[c] = seed + 1e-3 * c + 1e-9 * threadIdx.x;
+  for (int k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) x[c] = __fma_rn(x[c], mul, add);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += x[c];
+  if (s == -1.0) g_sink = s;
+}
+}  // namespace peak
+}  // namespace lbm
+
+extern "C" lbm_status lbm_fp64_fma_tflops(void *stream, double *tflops) {
+  if (!tflops) {
+    set_error("lbm_fp64_fma_tflops: NULL argument");
+    return LBM_EINVAL;
+  }
+  int dev = 0, sms = 1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail("lbm_fp64_fma_tflops", e);
+  cudaStream_t st = as_stream(stream);
+  const int blocks = 8 * sms, iters = 2048;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // first: warm-up
+    e = cudaEventRecord(e0, st);
+    peak::fp64_fma_kernel<<<blocks, peak::kThreads, 0, st>>>(iters, 0.5,
+                                                             0.9999999, 1e-8);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail("lbm_fp64_fma_tflops", e);
+  const double flops = 2.0 * peak::kChains * static_cast<double>(iters) *
+                       blocks * peak::kThreads;
+  *tflops = flops / (best * 1e-3) / 1e12;
+  return LBM_OK;
+}

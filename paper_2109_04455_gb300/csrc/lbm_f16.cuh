@@ -116,6 +116,10 @@ __device__ __forceinline__ __half round_half(float v, uint32_t h, int k) {
 #ifndef LBM_F16_SR_HW
 #define LBM_F16_SR_HW 1
 #endif
+// Load schedule of the two-node bulk step (see adr_bulk_pair_kernel)
+#ifndef LBM_F16_PIPE
+#define LBM_F16_PIPE 0
+#endif
 __device__ __forceinline__ __half2 round_pair(float lo, float hi, uint32_t h,
                                               int k) {
 #if LBM_F16_SR && LBM_F16_SR_HW
@@ -212,33 +216,44 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
     const __half *__restrict__ src = static_cast<const __half *>(a.src);
     __half *__restrict__ dst = static_cast<__half *>(a.dst);
     const __half2 z2 = __float2half2_rn(0.0f);
-    // all loads first: own pairs pc, side pairs pe (left for c_ix = +1,
-    // right for c_ix = -1), reference pairs of rows y - 1, y, y + 1
-    __half2 pc[NS][9], pe[NS][9], rc[NS][3], rl[NS][3], rr[NS][3];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
+    // Loads of one species into slot k: own pairs pc, side pairs pe (left
+    // for c_ix = +1, right for c_ix = -1), reference pairs of rows y - 1,
+    // y, y + 1.  LBM_F16_PIPE 0: every species' loads first (NS slots);
+    // 1: a species' loads just before its arithmetic (one slot); 2: the
+    // next species' loads issued before this one's arithmetic (two slots).
+    // Compiler barriers keep the loads where they are put, so fewer loaded
+    // values are live at once.
+    constexpr int SL = LBM_F16_PIPE == 0 ? NS : (LBM_F16_PIPE == 1 ? 1 : 2);
+    __half2 pc[SL][9], pe[SL][9], rc[SL][3], rl[SL][3], rr[SL][3];
+    auto load = [&](int sp, int k) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        const __half *row = src + (long long)(s * 9 + i) * plane +
+        const __half *row = src + (long long)(sp * 9 + i) * plane +
                             (long long)(y - cy(i)) * np + x0;
-        pc[s][i] = *reinterpret_cast<const __half2 *>(row);
-        if (cx(i) > 0) pe[s][i] = in0 ? *reinterpret_cast<const __half2 *>(row - 2) : z2;
-        if (cx(i) < 0) pe[s][i] = in1 ? *reinterpret_cast<const __half2 *>(row + 2) : z2;
+        pc[k][i] = *reinterpret_cast<const __half2 *>(row);
+        if (cx(i) > 0) pe[k][i] = in0 ? *reinterpret_cast<const __half2 *>(row - 2) : z2;
+        if (cx(i) < 0) pe[k][i] = in1 ? *reinterpret_cast<const __half2 *>(row + 2) : z2;
       }
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        const __half *row = a.rsrc + (long long)s * plane + (long long)(y + r - 1) * np + x0;
-        rc[s][r] = *reinterpret_cast<const __half2 *>(row);
-        rl[s][r] = in0 ? *reinterpret_cast<const __half2 *>(row - 2) : z2;
-        rr[s][r] = in1 ? *reinterpret_cast<const __half2 *>(row + 2) : z2;
+        const __half *row = a.rsrc + (long long)sp * plane + (long long)(y + r - 1) * np + x0;
+        rc[k][r] = *reinterpret_cast<const __half2 *>(row);
+        rl[k][r] = in0 ? *reinterpret_cast<const __half2 *>(row - 2) : z2;
+        rr[k][r] = in1 ? *reinterpret_cast<const __half2 *>(row + 2) : z2;
       }
+    };
+    if constexpr (LBM_F16_PIPE == 0) {
+#pragma unroll
+      for (int sp = 0; sp < NS; ++sp) load(sp, sp);
+    } else {
+      load(0, 0);
     }
     float *__restrict__ cp = static_cast<float *>(a.cprev);
     float2 prev[NS];
     if (MODE == kAdrCheck) {
 #pragma unroll
-      for (int s = 0; s < NS; ++s)
-        prev[s] = *reinterpret_cast<const float2 *>(cp + s * plane + n0);
+      for (int sp = 0; sp < NS; ++sp)
+        prev[sp] = *reinterpret_cast<const float2 *>(cp + sp * plane + n0);
     }
     const float *__restrict__ U = static_cast<const float *>(a.u);
     const float2 ux = *reinterpret_cast<const float2 *>(U + n0);
@@ -249,16 +264,24 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
     const uint32_t hp = f16::pair_hash(n0 >> 1, a.step);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
+      const int sl = LBM_F16_PIPE == 0 ? s : (LBM_F16_PIPE == 1 ? 0 : (s & 1));
+      if constexpr (LBM_F16_PIPE == 1) {
+        if (s > 0) load(s, 0);
+      }
+      if constexpr (LBM_F16_PIPE == 2) {
+        if (s + 1 < NS) load(s + 1, (s + 1) & 1);
+      }
+      if constexpr (LBM_F16_PIPE != 0) asm volatile("" ::: "memory");
       // references of the source columns x0 - 1 .. x0 + 2, rows
       // y - 1 .. y + 1 (the left / right column only where it is read)
       float rs[3][4];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        const float2 c2 = __half22float2(rc[s][r]);
-        rs[r][0] = __high2float(rl[s][r]);
+        const float2 c2 = __half22float2(rc[sl][r]);
+        rs[r][0] = __high2float(rl[sl][r]);
         rs[r][1] = c2.x;
         rs[r][2] = c2.y;
-        rs[r][3] = __low2float(rr[s][r]);
+        rs[r][3] = __low2float(rr[sl][r]);
       }
       float g0[9], g1[9];
 #pragma unroll
@@ -267,14 +290,14 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
         const int k = 1 - cx(i);      // column of node x0's source, x0 - 1 + k
         __half h0, h1;
         if (cx(i) == 0) {
-          h0 = __low2half(pc[s][i]);
-          h1 = __high2half(pc[s][i]);
+          h0 = __low2half(pc[sl][i]);
+          h1 = __high2half(pc[sl][i]);
         } else if (cx(i) > 0) {
-          h0 = __high2half(pe[s][i]);
-          h1 = __low2half(pc[s][i]);
+          h0 = __high2half(pe[sl][i]);
+          h1 = __low2half(pc[sl][i]);
         } else {
-          h0 = __high2half(pc[s][i]);
-          h1 = __low2half(pe[s][i]);
+          h0 = __high2half(pc[sl][i]);
+          h1 = __low2half(pe[sl][i]);
         }
         g0[i] = f16::pull(i, __half2float(h0), rs[r][k]);
         g1[i] = f16::pull(i, __half2float(h1), rs[r][k + 1]);
@@ -318,6 +341,7 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
         if (in0) check_add<NS, float>(acc[0], s, c0, prev[s].x);
         if (in1) check_add<NS, float>(acc[1], s, c1, prev[s].y);
       }
+      if constexpr (LBM_F16_PIPE != 0) asm volatile("" ::: "memory");
     }
   }
   if constexpr (MODE == kAdrCheck) {

@@ -92,7 +92,10 @@ struct Buf {
 };
 
 // Counters (device, unsigned long long): the particle count of each buffer,
-// the outflow of each species since the last reset, the overflow flag.
+// the outflow of each species since the last reset, the overflow flag.  A
+// buffer's count can pass the capacity when particles are dropped for lack
+// of room (the appends count them, the slots refuse them), so every reader
+// takes min(count, capacity).
 enum { kCount0 = 0, kCount1 = 1, kOut = 2, kOverflow = 5, kCounters = 8 };
 
 __device__ inline double dadd(double a, double b) { return __dadd_rn(a, b); }
@@ -200,7 +203,7 @@ __device__ inline long long warp_slot(bool keep, unsigned long long *cnt,
 __global__ void __launch_bounds__(kThreads)
     rwpt_step_kernel(const Args a, Buf in, Buf out, unsigned long long *cnt,
                      int kin, int kout, long long cap, long long t) {
-  const long long n = static_cast<long long>(cnt[kin]);
+  const long long n = min(static_cast<long long>(cnt[kin]), cap);
   const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
   for (long long base = static_cast<long long>(blockIdx.x) * blockDim.x; base < n;
        base += stride) {
@@ -560,7 +563,9 @@ extern "C" lbm_status lbm_rwpt_run(lbm_rwpt *r, int64_t nsteps, void *stream,
   std::memset(info, 0, sizeof(*info));
   info->steps = r->steps;
   info->window_steps = r->window;
-  info->alive = static_cast<int64_t>(h[kCount0 + r->cur]);
+  info->alive = static_cast<int64_t>(h[kCount0 + r->cur]) < r->cap
+                    ? static_cast<int64_t>(h[kCount0 + r->cur])
+                    : r->cap;
   for (int s = 0; s < 3; ++s) info->out[s] = static_cast<int64_t>(h[kOut + s]);
   info->overflow = h[kOverflow] ? 1 : 0;
   const int ns = r->p.nspecies;
@@ -602,6 +607,7 @@ extern "C" lbm_status lbm_rwpt_particles(lbm_rwpt *r, void *stream,
                                   cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return rfail("lbm_rwpt_particles", e);
+  if (static_cast<long long>(n) > r->cap) n = static_cast<unsigned long long>(r->cap);
   *count = static_cast<int64_t>(n);
   if (static_cast<long long>(n) > max_count) {
     set_error("lbm_rwpt_particles: host arrays shorter than the particle count");

@@ -120,6 +120,7 @@ _SIGS = {
     "lbm_adr_solve": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_size_t, _P, _P,
                                      _P]),
     "lbm_efficiency": (ctypes.c_int, [_P, ctypes.c_int32, _P]),
+    "lbm_fp64_fma_tflops": (ctypes.c_int, [_P, _P]),
     "lbm_adr_outflux_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "lbm_batch_ws_bytes": (ctypes.c_size_t, [ctypes.c_int32, _P, _P]),
     "lbm_batch_create": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, _P,
@@ -183,6 +184,13 @@ def _device_bytes(nbytes: int, device="cuda"):
     import torch
     # torch's caching allocator returns 512-byte aligned blocks
     return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def lbm_fp64_fma_tflops(stream=None) -> float:
+    """Measured FP64 FMA throughput of the current device (TFLOP/s)."""
+    v = ctypes.c_double()
+    _check(load().lbm_fp64_fma_tflops(_stream_ptr(stream), ctypes.byref(v)))
+    return v.value
 
 
 def lbm_efficiency(flux, nspecies: int) -> float:

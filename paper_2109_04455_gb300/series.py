@@ -76,6 +76,18 @@ def production_rate(flux, ny: int, nspecies: int) -> float:
 # ---------------------------------------------------------------------------
 DEFAULT_PE = (1.0, 2.0, 3.0, 5.0, 7.0, 10.0, 20.0, 30.0)
 TAU_MIN = 0.52
+# efficiency against Da at fixed Pe (Sec. IV.A, Fig. singleAB_Da)
+DA_SERIES_PE = (1.0, 7.0, 20.0)
+DA_SERIES = tuple(float(v) for v in np.logspace(-1, 3, 9))
+
+
+def da_workloads(pes=DA_SERIES_PE, das=DA_SERIES):
+    """The isolated A->B fiber at Pe = 1, 7, 20 over Da = 0.1 .. 1000 (the
+    values with k = Da D / R^2 < 1 per step)."""
+    out = [("isolated_fiber", inputs.isolated_fiber(pe, da))
+           for pe in pes for da in das]
+    return [(k, w) for k, w in out
+            if max(w.k1, w.k2) < 1.0 and w.tau_c >= TAU_MIN]
 
 
 def workloads(pes=DEFAULT_PE, xis=(2.0, 20.0, 100.0),
@@ -120,11 +132,12 @@ def solve_flows(items, flow_tol: float = 1e-9, flow_max: int = 400000,
 
 def run(items=None, flows=None, precision: int = lbm.LBM_F32,
         tol: float = 1e-6, max_steps: int = 200000, check_every: int = 1000,
-        device="cuda"):
+        device="cuda", flags: int = 0):
     """Steady efficiencies of the series.  Returns (rows, batches): one dict
     per lattice (geometry key, Pe, Da, eps, model eps where the paper gives
     one, production rate, steps, converged) and the Batch objects' launch
-    shapes."""
+    shapes.  flags: LBM_ADR_* bits for every lattice (LBM_ADR_NODEWISE: the
+    node-wise reaction the paper compares with in Fig. node_vs_pop)."""
     items = workloads() if items is None else items
     flows = solve_flows(items, device=device) if flows is None else flows
     rows = []
@@ -140,7 +153,8 @@ def run(items=None, flows=None, precision: int = lbm.LBM_F32,
             params.append(lbm.adr_params(ns, w.tau_c, w.c_in,
                                          precision=precision,
                                          max_steps=max_steps, tol=tol,
-                                         check_every=check_every))
+                                         check_every=check_every,
+                                         flags=flags))
             u = flows[key][0]
             us.append(u if precision == lbm.LBM_F64 else u.float())
         b = lbm.Batch(geoms, params, us, device)
