@@ -83,6 +83,12 @@ __device__ __forceinline__ float push(int i, float g, float e, const PushK &k) {
 #ifndef LBM_F16_SR
 #define LBM_F16_SR 1
 #endif
+// Hash of (node pair, step) for the random bits.  Its constants are
+// published integer-hash multipliers: 0x9E3779B1 (2^32 divided by the golden
+// ratio, Knuth's multiplicative hashing), 0x85EBCA77 (the second 32-bit
+// prime of xxHash), and the xor-shift-multiply finaliser with 0x7FEB352D,
+// 0x846CA68B and shifts 16 / 15 / 16 (the "lowbias32" hash found by
+// C. Wellons' hash prospector); 0x632BE5AB is an arbitrary odd offset.
 __device__ __forceinline__ uint32_t pair_hash(long long pair, unsigned step) {
   uint32_t h = static_cast<uint32_t>(pair) * 0x9E3779B1u ^
                static_cast<uint32_t>(pair >> 32) * 0x7FEB352Du ^
@@ -115,10 +121,6 @@ __device__ __forceinline__ __half round_half(float v, uint32_t h, int k) {
 // element by element.
 #ifndef LBM_F16_SR_HW
 #define LBM_F16_SR_HW 1
-#endif
-// Load schedule of the two-node bulk step (see adr_bulk_pair_kernel)
-#ifndef LBM_F16_PIPE
-#define LBM_F16_PIPE 0
 #endif
 __device__ __forceinline__ __half2 round_pair(float lo, float hi, uint32_t h,
                                               int k) {
@@ -189,7 +191,7 @@ __device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long lon
 // y.  Every plane is read as aligned half2 pairs.  A pull with c_ix = +1
 // takes the sources (x0 - 1, x0): the high half of the pair to the left and
 // the low half of the node's own pair; c_ix = -1 takes (x0 + 1, x0 + 2)
-// from the own pair and the pair to the right.  The left pair is read only
+// from the own pair and the pair to the right.  The left pair is needed only
 // when node x0 is interior (its neighbour x0 - 1 is a lattice node, so
 // x0 >= 2) and the right pair only when node x0 + 1 is interior (x0 + 2 <=
 // nx - 1, so x0 + 3 < nx_pad): every read stays inside its row, and rows
@@ -198,14 +200,149 @@ __device__ __forceinline__ void adr_interior_node_f16(const AdrArgs &a, long lon
 // pairs per species).  The arithmetic is that of adr_interior_node_f16.
 // Launched with kBlockX / 2 threads on the grid of adr_bulk_kernel, so a
 // block covers the same kBlockX nodes and writes the same partial-sum row.
+//
+// Each thread reads 24 pairs per species: slot 0..8 its own pair of plane
+// i, 9..14 the side pair of the six planes with c_ix != 0 (directions 1, 3,
+// 5, 6, 7, 8), 15..17 the centre reference pairs of rows y - 1, y, y + 1,
+// 18..20 the left ones, 21..23 the right ones.
 constexpr int kPairThreads = kBlockX / 2;
+constexpr int kPairSlots = 24;
+__device__ __forceinline__ constexpr int side_slot(int i) {
+  return i == 1 ? 9 : i == 3 ? 10 : i == 5 ? 11 : i == 6 ? 12 : i == 7 ? 13 : 14;
+}
+// global address of slot k of species s for the pair at (y, x0), and
+// whether the pair is needed (side pairs only for an interior neighbour)
+struct PairSrc {
+  const __half *p;
+  bool need;
+};
+__device__ __forceinline__ PairSrc pair_src(const AdrArgs &a, int s, int k,
+                                            int y, int x0, bool in0, bool in1) {
+  const long long np = a.nx_pad, plane = a.plane;
+  const __half *src = static_cast<const __half *>(a.src);
+  if (k < 9) {
+    return {src + (long long)(s * 9 + k) * plane + (long long)(y - cy(k)) * np + x0,
+            true};
+  }
+  if (k < 15) {
+    const int i = k == 9 ? 1 : k == 10 ? 3 : k == 11 ? 5 : k == 12 ? 6 : k == 13 ? 7 : 8;
+    const __half *row = src + (long long)(s * 9 + i) * plane + (long long)(y - cy(i)) * np + x0;
+    return cx(i) > 0 ? PairSrc{row - 2, in0} : PairSrc{row + 2, in1};
+  }
+  const int r = (k - 15) % 3, side = (k - 15) / 3;   // 0 centre, 1 left, 2 right
+  const __half *row = a.rsrc + (long long)s * plane + (long long)(y + r - 1) * np + x0;
+  return side == 0 ? PairSrc{row, true} : side == 1 ? PairSrc{row - 2, in0}
+                                                   : PairSrc{row + 2, in1};
+}
+
+// The update of the pair from its 24 x NS source pairs, fetched by
+// fetch(s, k) (k as above; a side pair that is not needed may hold
+// anything).  Stores the new populations, references and, on check steps,
+// the recorded concentrations, and adds the check-step values to acc.
+template <int NS, int MODE, class Fetch>
+__device__ __forceinline__ void pair_update(const AdrArgs &a, int y, int x0,
+                                            bool in0, bool in1, Fetch &&fetch,
+                                            float (&acc)[2][3 * NS]) {
+  const long long np = a.nx_pad, plane = a.plane;
+  const long long n0 = (long long)y * np + x0;
+  __half *__restrict__ dst = static_cast<__half *>(a.dst);
+  float *__restrict__ cp = static_cast<float *>(a.cprev);
+  float2 prev[NS];
+  if (MODE == kAdrCheck) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      prev[s] = *reinterpret_cast<const float2 *>(cp + s * plane + n0);
+  }
+  const float *__restrict__ U = static_cast<const float *>(a.u);
+  const float2 ux = *reinterpret_cast<const float2 *>(U + n0);
+  const float2 uy = *reinterpret_cast<const float2 *>(U + plane + n0);
+  float E0[9], E1[9];
+  f16::eq(ux.x, uy.x, E0);
+  f16::eq(ux.y, uy.y, E1);
+  const uint32_t hp = f16::pair_hash(n0 >> 1, a.step);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    // references of the source columns x0 - 1 .. x0 + 2, rows
+    // y - 1 .. y + 1 (the left / right column only where it is read)
+    float rs[3][4];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float2 c2 = __half22float2(fetch(s, 15 + r));
+      rs[r][0] = __high2float(fetch(s, 18 + r));
+      rs[r][1] = c2.x;
+      rs[r][2] = c2.y;
+      rs[r][3] = __low2float(fetch(s, 21 + r));
+    }
+    float g0[9], g1[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int r = 1 - cy(i);      // source row y - cy(i)
+      const int k = 1 - cx(i);      // column of node x0's source, x0 - 1 + k
+      const __half2 own = fetch(s, i);
+      __half h0, h1;
+      if (cx(i) == 0) {
+        h0 = __low2half(own);
+        h1 = __high2half(own);
+      } else if (cx(i) > 0) {
+        h0 = __high2half(fetch(s, side_slot(i)));
+        h1 = __low2half(own);
+      } else {
+        h0 = __high2half(own);
+        h1 = __low2half(fetch(s, side_slot(i)));
+      }
+      g0[i] = f16::pull(i, __half2float(h0), rs[r][k]);
+      g1[i] = f16::pull(i, __half2float(h1), rs[r][k + 1]);
+    }
+    const float cs0 = f16::sum9(g0), cs1 = f16::sum9(g1);
+    const float c0 = __fmul_rn(cs0, f16::kDown), c1 = __fmul_rn(cs1, f16::kDown);
+    const float cq0 = __fmul_rn(ref_round(c0), f16::kUp);
+    const float cq1 = __fmul_rn(ref_round(c1), f16::kUp);
+    const float om = a.fomega[s];
+    const f16::PushK k0 = f16::push_k(om, cs0, cq0);
+    const f16::PushK k1 = f16::push_k(om, cs1, cq1);
+    __half *o = dst + (long long)s * 9 * plane + n0;
+    __half *ro = a.rdst + (long long)s * plane + n0;
+    float *co = cp + s * plane + n0;
+    if (in0 && in1) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        *reinterpret_cast<__half2 *>(o + (long long)i * plane) = f16::round_pair(
+            f16::push(i, g0[i], E0[i], k0), f16::push(i, g1[i], E1[i], k1), hp,
+            s * 9 + i);
+      *reinterpret_cast<__half2 *>(ro) = __floats2half2_rn(c0, c1);
+      if (MODE == kAdrCheck) *reinterpret_cast<float2 *>(co) = make_float2(c0, c1);
+    } else {
+      // one interior node: the other belongs to the boundary kernel
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const __half2 r2 = f16::round_pair(
+            in0 ? f16::push(i, g0[i], E0[i], k0) : 0.0f,
+            in1 ? f16::push(i, g1[i], E1[i], k1) : 0.0f, hp, s * 9 + i);
+        if (in0) o[(long long)i * plane] = __low2half(r2);
+        if (in1) o[(long long)i * plane + 1] = __high2half(r2);
+      }
+      if (in0) ro[0] = __float2half_rn(c0);
+      if (in1) ro[1] = __float2half_rn(c1);
+      if (MODE == kAdrCheck) {
+        if (in0) co[0] = c0;
+        if (in1) co[1] = c1;
+      }
+    }
+    if (MODE == kAdrCheck) {
+      if (in0) check_add<NS, float>(acc[0], s, c0, prev[s].x);
+      if (in1) check_add<NS, float>(acc[1], s, c1, prev[s].y);
+    }
+  }
+}
+
+// Register-staged form: the thread loads its 24 x NS pairs into registers,
+// all before any arithmetic (so they are in flight together).
 template <int NS, int MODE>
 __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
     adr_bulk_pair_kernel(const AdrArgs a) {
-  const long long np = a.nx_pad, plane = a.plane;
   const int y = blockIdx.y;
   const int x0 = 2 * (blockIdx.x * kPairThreads + threadIdx.x);
-  const long long n0 = (long long)y * np + x0;
+  const long long n0 = (long long)y * a.nx_pad + x0;
   uint2 lw = make_uint2(kSolidNode, kSolidNode);
   if (x0 < a.nx_pad) lw = *reinterpret_cast<const uint2 *>(a.links + n0);
   const bool in0 = lw.x == 0u, in1 = lw.y == 0u;
@@ -213,136 +350,18 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
 #pragma unroll
   for (int k = 0; k < 3 * NS; ++k) acc[0][k] = acc[1][k] = 0.0f;
   if (in0 || in1) {
-    const __half *__restrict__ src = static_cast<const __half *>(a.src);
-    __half *__restrict__ dst = static_cast<__half *>(a.dst);
     const __half2 z2 = __float2half2_rn(0.0f);
-    // Loads of one species into slot k: own pairs pc, side pairs pe (left
-    // for c_ix = +1, right for c_ix = -1), reference pairs of rows y - 1,
-    // y, y + 1.  LBM_F16_PIPE 0: every species' loads first (NS slots);
-    // 1: a species' loads just before its arithmetic (one slot); 2: the
-    // next species' loads issued before this one's arithmetic (two slots).
-    // Compiler barriers keep the loads where they are put, so fewer loaded
-    // values are live at once.
-    constexpr int SL = LBM_F16_PIPE == 0 ? NS : (LBM_F16_PIPE == 1 ? 1 : 2);
-    __half2 pc[SL][9], pe[SL][9], rc[SL][3], rl[SL][3], rr[SL][3];
-    auto load = [&](int sp, int k) {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const __half *row = src + (long long)(sp * 9 + i) * plane +
-                            (long long)(y - cy(i)) * np + x0;
-        pc[k][i] = *reinterpret_cast<const __half2 *>(row);
-        if (cx(i) > 0) pe[k][i] = in0 ? *reinterpret_cast<const __half2 *>(row - 2) : z2;
-        if (cx(i) < 0) pe[k][i] = in1 ? *reinterpret_cast<const __half2 *>(row + 2) : z2;
-      }
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const __half *row = a.rsrc + (long long)sp * plane + (long long)(y + r - 1) * np + x0;
-        rc[k][r] = *reinterpret_cast<const __half2 *>(row);
-        rl[k][r] = in0 ? *reinterpret_cast<const __half2 *>(row - 2) : z2;
-        rr[k][r] = in1 ? *reinterpret_cast<const __half2 *>(row + 2) : z2;
-      }
-    };
-    if constexpr (LBM_F16_PIPE == 0) {
-#pragma unroll
-      for (int sp = 0; sp < NS; ++sp) load(sp, sp);
-    } else {
-      load(0, 0);
-    }
-    float *__restrict__ cp = static_cast<float *>(a.cprev);
-    float2 prev[NS];
-    if (MODE == kAdrCheck) {
-#pragma unroll
-      for (int sp = 0; sp < NS; ++sp)
-        prev[sp] = *reinterpret_cast<const float2 *>(cp + sp * plane + n0);
-    }
-    const float *__restrict__ U = static_cast<const float *>(a.u);
-    const float2 ux = *reinterpret_cast<const float2 *>(U + n0);
-    const float2 uy = *reinterpret_cast<const float2 *>(U + plane + n0);
-    float E0[9], E1[9];
-    f16::eq(ux.x, uy.x, E0);
-    f16::eq(ux.y, uy.y, E1);
-    const uint32_t hp = f16::pair_hash(n0 >> 1, a.step);
+    __half2 v[NS][kPairSlots];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      const int sl = LBM_F16_PIPE == 0 ? s : (LBM_F16_PIPE == 1 ? 0 : (s & 1));
-      if constexpr (LBM_F16_PIPE == 1) {
-        if (s > 0) load(s, 0);
-      }
-      if constexpr (LBM_F16_PIPE == 2) {
-        if (s + 1 < NS) load(s + 1, (s + 1) & 1);
-      }
-      if constexpr (LBM_F16_PIPE != 0) asm volatile("" ::: "memory");
-      // references of the source columns x0 - 1 .. x0 + 2, rows
-      // y - 1 .. y + 1 (the left / right column only where it is read)
-      float rs[3][4];
 #pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        const float2 c2 = __half22float2(rc[sl][r]);
-        rs[r][0] = __high2float(rl[sl][r]);
-        rs[r][1] = c2.x;
-        rs[r][2] = c2.y;
-        rs[r][3] = __low2float(rr[sl][r]);
+      for (int k = 0; k < kPairSlots; ++k) {
+        const PairSrc q = pair_src(a, s, k, y, x0, in0, in1);
+        v[s][k] = q.need ? *reinterpret_cast<const __half2 *>(q.p) : z2;
       }
-      float g0[9], g1[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const int r = 1 - cy(i);      // source row y - cy(i)
-        const int k = 1 - cx(i);      // column of node x0's source, x0 - 1 + k
-        __half h0, h1;
-        if (cx(i) == 0) {
-          h0 = __low2half(pc[sl][i]);
-          h1 = __high2half(pc[sl][i]);
-        } else if (cx(i) > 0) {
-          h0 = __high2half(pe[sl][i]);
-          h1 = __low2half(pc[sl][i]);
-        } else {
-          h0 = __high2half(pc[sl][i]);
-          h1 = __low2half(pe[sl][i]);
-        }
-        g0[i] = f16::pull(i, __half2float(h0), rs[r][k]);
-        g1[i] = f16::pull(i, __half2float(h1), rs[r][k + 1]);
-      }
-      const float cs0 = f16::sum9(g0), cs1 = f16::sum9(g1);
-      const float c0 = __fmul_rn(cs0, f16::kDown), c1 = __fmul_rn(cs1, f16::kDown);
-      const float cq0 = __fmul_rn(ref_round(c0), f16::kUp);
-      const float cq1 = __fmul_rn(ref_round(c1), f16::kUp);
-      const float om = a.fomega[s];
-      const f16::PushK k0 = f16::push_k(om, cs0, cq0);
-      const f16::PushK k1 = f16::push_k(om, cs1, cq1);
-      __half *o = dst + (long long)s * 9 * plane + n0;
-      __half *ro = a.rdst + (long long)s * plane + n0;
-      float *co = cp + s * plane + n0;
-      if (in0 && in1) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i)
-          *reinterpret_cast<__half2 *>(o + (long long)i * plane) = f16::round_pair(
-              f16::push(i, g0[i], E0[i], k0), f16::push(i, g1[i], E1[i], k1), hp,
-              s * 9 + i);
-        *reinterpret_cast<__half2 *>(ro) = __floats2half2_rn(c0, c1);
-        if (MODE == kAdrCheck) *reinterpret_cast<float2 *>(co) = make_float2(c0, c1);
-      } else {
-        // one interior node: the other belongs to the boundary kernel
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const __half2 r2 = f16::round_pair(
-              in0 ? f16::push(i, g0[i], E0[i], k0) : 0.0f,
-              in1 ? f16::push(i, g1[i], E1[i], k1) : 0.0f, hp, s * 9 + i);
-          if (in0) o[(long long)i * plane] = __low2half(r2);
-          if (in1) o[(long long)i * plane + 1] = __high2half(r2);
-        }
-        if (in0) ro[0] = __float2half_rn(c0);
-        if (in1) ro[1] = __float2half_rn(c1);
-        if (MODE == kAdrCheck) {
-          if (in0) co[0] = c0;
-          if (in1) co[1] = c1;
-        }
-      }
-      if (MODE == kAdrCheck) {
-        if (in0) check_add<NS, float>(acc[0], s, c0, prev[s].x);
-        if (in1) check_add<NS, float>(acc[1], s, c1, prev[s].y);
-      }
-      if constexpr (LBM_F16_PIPE != 0) asm volatile("" ::: "memory");
     }
+    pair_update<NS, MODE>(a, y, x0, in0, in1,
+                          [&](int s, int k) { return v[s][k]; }, acc);
   }
   if constexpr (MODE == kAdrCheck) {
     const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
