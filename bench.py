@@ -17,7 +17,7 @@ carries, unless --no-extra: the other two precisions timed the same way
 its FP64 arithmetic against the FMA rate measured on the same GPU by
 lbm_fp64_fma_tflops), and an efficiency check at equal step counts: FP32
 and FP16 storage against FP64 on the full lattice, outfluxes on a plane
-64 nodes behind the first (A->B) membrane.
+through the middle of the first (A->B) membrane.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f16dev|f64]
 python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
@@ -90,6 +90,10 @@ def _args():
                          "runs every instance exactly --sweep-max-steps "
                          "steps in every precision")
     ap.add_argument("--sweep-flow-steps", type=int, default=3000)
+    ap.add_argument("--sweep-mode", default="fixed", choices=["fixed", "steady"],
+                    help="fixed: every instance a fixed step count in every "
+                         "precision; steady: every instance to its steady "
+                         "state (residual and efficiency tests)")
     ap.add_argument("--fd-steps", type=int, default=150000,
                     help="adjoint-check: steps of each perturbed solve "
                          "after the base state")
@@ -452,7 +456,7 @@ def _measure(precision, geom, w, u, steps, warmup, dev, world, fp64_peak):
 def _eps_check(geom, w, u64, steps, plane, dev):
     """FP32 and FP16 storage against FP64 on the full lattice at equal step
     counts from the same start on the same FP64 flow: outfluxes on a plane
-    behind the first (A->B) membrane, where B made there crosses.  Reports
+    through the first (A->B) membrane, where B is made.  Reports
     each precision's fluxes, the A->B efficiency N_B / (N_A + N_B) on that
     plane, the cascade efficiency of Eq. (A-B) (N_C / sum N) and the
     differences to FP64."""
@@ -561,7 +565,10 @@ def run_gpu(a):
             del sv
             torch.cuda.empty_cache()
             others[name] = rec
-        plane = int(round(2 * w.nx / 9.0)) + 64
+        # the middle of the first (A->B) membrane: B is made there from the
+        # first step (at Da = 0.5 the rate is 6e-5 per step, and B made in
+        # the band has not crossed a plane behind it within these steps)
+        plane = int(round(1.5 * w.nx / 9.0))
         eps_check = _eps_check(geom, w, u64, a.eps_steps, plane, dev)
 
     if rank == 0:
@@ -597,6 +604,93 @@ def run_gpu(a):
 # ---------------------------------------------------------------------------
 # Pe x Da sweep: batched reduced precision against unbatched FP64
 # ---------------------------------------------------------------------------
+def run_sweep_steady(a):
+    """The Pe x Da sweep to steady state.  Untimed: each instance's flow in
+    FP64 to a per-step residual of 1e-8.  Timed (CUDA events): every
+    instance's ADR solve to its steady state, judged by the per-step
+    residual and by the efficiency test (eps_tol: Aitken's extrapolation of
+    the last three checks, every 1000 steps): FP64 one lbm_adr_solve per
+    instance (residual 1e-9, eps settled to 1e-7: the reference), FP32 the
+    same way and in one batch (residual 1e-6, eps 1e-5), FP16 storage in one
+    batch (residual 1e-5, above its stochastic-rounding floor; eps 1e-5).
+    Reports solves/s, steps, and the largest |eps - eps_FP64| of each."""
+    import torch
+
+    from paper_2109_04455_gb300 import inputs, lbm
+    torch.cuda.set_device(0)
+    ws_all = [inputs.sweep_instance(i) for i in range(a.sweep_instances)]
+    ws = [w for w in ws_all if max(w.k1, w.k2) < 1.0]
+    geoms, u64 = [], []
+    t0 = time.perf_counter()
+    flow_steps = 0
+    for w in ws:
+        g = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
+        u, fi = lbm.lbm_flow_solve(g, w.tau_flow, w.u0, 1000000, tol=1e-8,
+                                   check_every=1000, precision=lbm.LBM_F64)
+        flow_steps += fi["steps"]
+        geoms.append(g)
+        u64.append(u)
+    flow_s = time.perf_counter() - t0
+    u32 = [u.float() for u in u64]
+    cap, check = a.sweep_max_steps, 1000
+
+    def params(prec, tol, eps_tol):
+        return [lbm.adr_params(3, w.tau_c, precision=prec, max_steps=cap,
+                               tol=tol, eps_tol=eps_tol, check_every=check)
+                for w in ws]
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
+        enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev0.record()
+        out = fn()
+        ev1.record()
+        torch.cuda.synchronize()
+        return out, ev0.elapsed_time(ev1) * 1e-3
+
+    res = {}
+    ref, t64 = timed(lambda: [lbm.lbm_adr_solve(g, p, u, want_conc=False)[1]
+                              for g, p, u in zip(geoms, params(
+                                  lbm.LBM_F64, 1e-9, 1e-7), u64)])
+    res["f64_unbatched"] = (ref, t64)
+    r32, t32 = timed(lambda: [lbm.lbm_adr_solve(g, p, u, want_conc=False)[1]
+                              for g, p, u in zip(geoms, params(
+                                  lbm.LBM_F32, 1e-6, 1e-5), u32)])
+    res["f32_unbatched"] = (r32, t32)
+    for name, prec, tol in (("f32_batched", lbm.LBM_F32, 1e-6),
+                            ("f16dev_batched", lbm.LBM_F16DEV, 1e-5)):
+        b = lbm.Batch(geoms, params(prec, tol, 1e-5), u32)
+        b.tune()
+        infos, t = timed(lambda: b.solve())
+        b.close()
+        res[name] = (infos, t)
+    out = {"metric": "Pe x Da sweep solves/s to steady state (ADR, 3 species)",
+           "unit": "solves/s", "higher_is_better": True,
+           "instances": len(ws), "left_out_k_ge_1": len(ws_all) - len(ws),
+           "nodes": sum(w.nx * w.ny for w in ws), "step_cap": cap,
+           "check_every": check, "flow": {"steps": flow_steps,
+                                          "seconds_untimed": flow_s}}
+    for name, (infos, t) in res.items():
+        errs = [abs(i["eps"] - r["eps"]) for i, r in zip(infos, ref)]
+        out[name] = {"solves_per_s": len(ws) / t, "seconds": t,
+                     "speedup_vs_f64": t64 / t,
+                     "converged": sum(bool(i["converged"]) for i in infos),
+                     "steps": sum(i["steps"] for i in infos),
+                     "max_abs_eps_err_vs_f64": max(errs),
+                     "instances_over_1e-3": sum(e > 1e-3 for e in errs)}
+    out["per_instance"] = [
+        {"pe": round(w.pe, 4), "da": round(w.da1, 4), "nx": w.nx, "ny": w.ny,
+         "eps_f64": r["eps"], "steps_f64": r["steps"],
+         "err_f32": abs(res["f32_batched"][0][k]["eps"] - r["eps"]),
+         "err_f16": abs(res["f16dev_batched"][0][k]["eps"] - r["eps"]),
+         "steps_f32": res["f32_batched"][0][k]["steps"],
+         "steps_f16": res["f16dev_batched"][0][k]["steps"]}
+        for k, (w, r) in enumerate(zip(ws, ref))]
+    print(json.dumps(out), flush=True)
+
+
 def run_sweep(a):
     """64 seeded lattices (Pe = logspace(-1,2,8) x Da = logspace(-2,2,8),
     widths 512..2048, heights 256..512), each with its own flow (FP64, fixed
@@ -1039,7 +1133,10 @@ def main():
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "sweep":
-        run_sweep(a)
+        if a.sweep_mode == "steady":
+            run_sweep_steady(a)
+        else:
+            run_sweep(a)
     elif a.workload == "adjoint":
         run_adjoint(a)
     elif a.workload == "series":

@@ -215,6 +215,18 @@ typedef struct {
                           < -neg_tol * max(1, c_in[0..nspecies)); 0 selects
                           0.1, < 0 turns the test off (c_min is reported
                           either way)                                        */
+  double eps_tol;      /* lbm_adr_solve / lbm_batch_solve, > 0: a lattice
+                          converges only when, besides residual < tol, the
+                          distance of its efficiency to the steady value is
+                          estimated below eps_tol: Aitken's delta-squared
+                          extrapolation of the last three checks, e1, e2,
+                          e3 with d1 = e2 - e1, d2 = e3 - e2 and
+                          q = d2 / d1 in [0, 1), gives |d2| / (1 - q)
+                          (changes that do not contract count as not
+                          converged unless both are below eps_tol / 10,
+                          the noise of reduced precisions).  A per-step
+                          residual alone is a poor steady-state test where
+                          diffusion dominates (low Pe).  <= 0: off         */
 } lbm_adr_params;
 
 /* Device bytes of the ADR workspace (two population buffers, the

@@ -31,6 +31,7 @@ struct AdjArgs {
   long long plane;
   int nx, ny, nx_pad, xp;
   int abb_all;
+  int periodic;             // the geometry has periodic edges (kPeriodic links)
   double omega[3];
   double dN[3];             // d eps / d N_s
   float fomega[3], fdN[3];  // the same in float
@@ -38,8 +39,10 @@ struct AdjArgs {
 
 enum AdjMode { kAdjStep = 0, kAdjCheck = 1 };
 
-// mu = P^T nu + l of species s at fluid node n = y nx_pad + x (link word lw)
-template <typename T>
+// mu = P^T nu + l of species s at fluid node n = y nx_pad + x (link word lw).
+// PER: the geometry may have periodic links (wrapped neighbours); without
+// them the gather keeps the plain shifts and fewer registers.
+template <typename T, bool PER>
 __device__ __forceinline__ void adj_gather(const AdjArgs &a, int s, uint32_t lw,
                                            long long n, int x, int y, T (&mu)[9]) {
   const T *nu = static_cast<const T *>(a.src) + (long long)s * 9 * a.plane;
@@ -51,7 +54,7 @@ __device__ __forceinline__ void adj_gather(const AdjArgs &a, int s, uint32_t lw,
     const uint32_t t = lw == 0u ? (uint32_t)kFluid : nib(lw, i);
     if (t == kFluid) {
       mu[i] = nu[(long long)i * plane + n + cy(i) * np + cx(i)];
-    } else if (t == kPeriodic) {
+    } else if (PER && t == kPeriodic) {
       mu[i] = nu[(long long)i * plane + neighbour(x, y, i, a.nx, a.ny, np)];
     } else {
       const T back = nu[(long long)opp(i) * plane + n];
@@ -120,7 +123,7 @@ __device__ __forceinline__ void adj_eq(const AdjArgs &a, long long n, T (&E)[9])
 // fluid, no source, no inlet or outlet) take a branch-free path that issues
 // all NS*9 gathered loads before any arithmetic; boundary nodes go through
 // adj_gather's link rules.  Both give the same values for an interior node.
-template <typename T, int NS, int MODE>
+template <typename T, int NS, int MODE, bool PER>
 __global__ void __launch_bounds__(kBlockX) adj_kernel(const AdjArgs a) {
   const int x = blockIdx.x * kBlockX + threadIdx.x;
   const int y = blockIdx.y;
@@ -157,7 +160,7 @@ __global__ void __launch_bounds__(kBlockX) adj_kernel(const AdjArgs a) {
     adj_eq<T>(a, n, E);
     T mu[NS][9];
 #pragma unroll
-    for (int s = 0; s < NS; ++s) adj_gather<T>(a, s, lw, n, x, y, mu[s]);
+    for (int s = 0; s < NS; ++s) adj_gather<T, PER>(a, s, lw, n, x, y, mu[s]);
     T R[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) R[s] = T(0);
@@ -165,7 +168,8 @@ __global__ void __launch_bounds__(kBlockX) adj_kernel(const AdjArgs a) {
 #pragma unroll
     for (int j = 1; j < 9; ++j) {
       if (nib(lw, j) != kCat) continue;
-      const long long m = neighbour(x, y, j, a.nx, a.ny, np);
+      const long long m = PER ? neighbour(x, y, j, a.nx, a.ny, np)
+                              : n + cy(j) * np + cx(j);
       const T wj = Lattice<T>::w(j);
       const T ka = T(a.kab[m]) * wj;
       R[0] += ka * ((NS >= 2 ? mu[NS >= 2 ? 1 : 0][j] : T(0)) - mu[0][j]);
@@ -201,7 +205,7 @@ __global__ void __launch_bounds__(kBlockX)
   const int y = static_cast<int>(n / a.nx_pad);
   T mu[NS][9];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) adj_gather<T>(a, s, lw, n, x, y, mu[s]);
+  for (int s = 0; s < NS; ++s) adj_gather<T, true>(a, s, lw, n, x, y, mu[s]);
   const T cA = conc[n];
   const T cB = NS >= 2 ? conc[a.plane + n] : T(0);
   const long long np = a.nx_pad;

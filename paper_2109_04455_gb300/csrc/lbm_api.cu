@@ -727,7 +727,8 @@ extern "C" lbm_status lbm_adr_solve(const lbm_geometry *g,
                                     void *ws, size_t ws_bytes, void *conc_out,
                                     void *stream, lbm_solve_info *info) {
   NvtxRange nvtx_range("lbm_adr_solve");
-  if (!p || p->max_steps < 2 || (p->tol > 0 && p->check_every < 2)) {
+  if (!p || p->max_steps < 2 ||
+      ((p->tol > 0 || p->eps_tol > 0) && p->check_every < 2)) {
     set_error("lbm_adr_solve: need max_steps >= 2 and check_every >= 2");
     return LBM_EINVAL;
   }
@@ -737,14 +738,26 @@ extern "C" lbm_status lbm_adr_solve(const lbm_geometry *g,
   st = lbm_adr_init(s, stream);
   lbm_solve_info loc{};
   if (st == LBM_OK) {
-    if (p->tol <= 0) {
+    if (p->tol <= 0 && p->eps_tol <= 0) {
       st = lbm_adr_run(s, p->max_steps, stream, &loc);
     } else {
+      double hist[3] = {NAN, NAN, NAN};   // efficiency at the last checks
+      int nh = 0;
       while (true) {
         const int64_t left = p->max_steps - s->steps;
         const int64_t n = left < p->check_every ? left : p->check_every;
         st = lbm_adr_run(s, n < 2 ? 2 : n, stream, &loc);
-        if (st != LBM_OK || loc.converged) break;
+        if (st != LBM_OK) break;
+        hist[0] = hist[1];
+        hist[1] = hist[2];
+        hist[2] = loc.eps;
+        ++nh;
+        bool conv = p->tol <= 0 || loc.residual < p->tol;
+        if (conv && p->eps_tol > 0)
+          conv = nh >= 3 && eps_distance(hist[0], hist[1], hist[2],
+                                         0.1 * p->eps_tol) < p->eps_tol;
+        loc.converged = conv ? 1 : 0;
+        if (conv) break;
         if (s->steps >= p->max_steps) {
           set_error("lbm_adr_solve: not converged within max_steps");
           st = LBM_ENOTCONVERGED;
@@ -892,6 +905,7 @@ extern "C" lbm_status lbm_adr_adjoint(lbm_adr_solver *s, int64_t max_steps,
   a.nx_pad = g->nx_pad;
   a.xp = s->p.x_plane < 0 ? g->nx - 3 : s->p.x_plane;
   a.abb_all = s->a.abb_all;
+  a.periodic = g->periodic != 0 ? 1 : 0;
   for (int k = 0; k < 3; ++k) {
     a.omega[k] = s->a.omega[k];
     a.dN[k] = dN[k];

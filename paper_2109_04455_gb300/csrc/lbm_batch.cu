@@ -235,6 +235,8 @@ struct lbm_batch {
   int parity = 0;
   std::vector<char> active;
   std::vector<int64_t> steps;
+  std::vector<double> eps_hist;         // [count][3] efficiency at the checks
+  std::vector<int> nhist;
   int check_every = 100;
   // launch shape (autotuned)
   int bx = 256;
@@ -655,6 +657,8 @@ extern "C" lbm_status lbm_batch_solve(lbm_batch *b, void *stream,
   if (s != LBM_OK) return s;
   b->solved = true;
   std::fill(b->active.begin(), b->active.end(), 1);
+  b->eps_hist.assign(3 * b->count, NAN);
+  b->nhist.assign(b->count, 0);
   std::memset(infos, 0, sizeof(lbm_solve_info) * b->count);
   const int ns = b->ns;
   std::vector<double> sums(3 * ns * b->count), flux(3 * b->count);
@@ -703,7 +707,16 @@ extern "C" lbm_status lbm_batch_solve(lbm_batch *b, void *stream,
       double eps = 0.0;
       if (lbm_efficiency(inf.flux, ns, &eps) == LBM_OK) inf.eps = eps;
       const bool negative = finite && adr_negative(&p, inf.c_min);
-      const bool conv = finite && !negative && p.tol > 0 && r < p.tol;
+      double *eh = &b->eps_hist[3 * (size_t)i];
+      eh[0] = eh[1];
+      eh[1] = eh[2];
+      eh[2] = inf.eps;
+      ++b->nhist[i];
+      bool conv = finite && !negative && (p.tol > 0 || p.eps_tol > 0) &&
+                  (p.tol <= 0 || r < p.tol);
+      if (conv && p.eps_tol > 0)
+        conv = b->nhist[i] >= 3 &&
+               eps_distance(eh[0], eh[1], eh[2], 0.1 * p.eps_tol) < p.eps_tol;
       inf.converged = conv ? 1 : 0;
       if (!finite) {
         result = LBM_EUNSTABLE;
@@ -717,7 +730,8 @@ extern "C" lbm_status lbm_batch_solve(lbm_batch *b, void *stream,
       if (conv || !finite || negative || b->steps[i] >= p.max_steps) {
         b->active[i] = 0;
         rebuild = true;
-        if (!conv && finite && !negative && p.tol > 0 && result == LBM_OK)
+        if (!conv && finite && !negative && (p.tol > 0 || p.eps_tol > 0) &&
+            result == LBM_OK)
           result = LBM_ENOTCONVERGED;
       }
     }

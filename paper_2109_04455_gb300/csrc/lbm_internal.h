@@ -39,6 +39,21 @@ void set_error(const std::string &msg);
 
 // True when some species' most negative concentration c_min[s] is below
 // -neg_tol * max(1, c_in) (neg_tol 0 selects 0.1, < 0 disables the test).
+// Estimated distance of the efficiency to its steady value from the last
+// three checks (Aitken's delta-squared extrapolation of a geometric
+// approach): |d2| / (1 - q), q = d2 / d1; infinite when the changes do not
+// contract, unless both are below `floor` (noise of reduced precisions).
+inline double eps_distance(double e1, double e2, double e3, double floor) {
+  const double d1 = e2 - e1, d2 = e3 - e2;
+  if (d2 == 0.0) return 0.0;
+  if (d1 != 0.0) {
+    const double q = d2 / d1;
+    if (q >= 0.0 && q < 1.0) return (d2 < 0 ? -d2 : d2) / (1.0 - q);
+  }
+  const double a1 = d1 < 0 ? -d1 : d1, a2 = d2 < 0 ? -d2 : d2;
+  return (a1 < floor && a2 < floor) ? (a1 > a2 ? a1 : a2) : 1e300;
+}
+
 inline bool adr_negative(const lbm_adr_params *p, const double *c_min) {
   if (p->neg_tol < 0) return false;
   const double tol = p->neg_tol > 0 ? p->neg_tol : 0.1;

@@ -111,10 +111,17 @@ cudaError_t launch_adjoint(int ns, int mode, const AdjArgs &a, cudaStream_t st) 
   const dim3 grid = adr_node_grid(a.nx_pad, a.ny);
 #define LBM_ADJ_CASE(NS)                                                  \
   if (ns == NS) {                                                         \
-    if (mode == kAdjCheck)                                                \
-      adj_kernel<T, NS, kAdjCheck><<<grid, block, 0, st>>>(a);            \
-    else                                                                  \
-      adj_kernel<T, NS, kAdjStep><<<grid, block, 0, st>>>(a);             \
+    if (mode == kAdjCheck) {                                              \
+      if (a.periodic)                                                     \
+        adj_kernel<T, NS, kAdjCheck, true><<<grid, block, 0, st>>>(a);    \
+      else                                                                \
+        adj_kernel<T, NS, kAdjCheck, false><<<grid, block, 0, st>>>(a);   \
+    } else {                                                              \
+      if (a.periodic)                                                     \
+        adj_kernel<T, NS, kAdjStep, true><<<grid, block, 0, st>>>(a);     \
+      else                                                                \
+        adj_kernel<T, NS, kAdjStep, false><<<grid, block, 0, st>>>(a);    \
+    }                                                                     \
     return cudaGetLastError();                                            \
   }
   LBM_ADJ_CASE(1)

@@ -65,7 +65,8 @@ class lbm_adr_params(ctypes.Structure):
                 ("tau", ctypes.c_double * 3), ("c_in", ctypes.c_double * 3),
                 ("max_steps", ctypes.c_int64), ("tol", ctypes.c_double),
                 ("check_every", ctypes.c_int32), ("x_plane", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("neg_tol", ctypes.c_double)]
+                ("flags", ctypes.c_int32), ("neg_tol", ctypes.c_double),
+                ("eps_tol", ctypes.c_double)]
 
 
 class lbm_rwpt_params(ctypes.Structure):
@@ -321,16 +322,19 @@ def lbm_flow_solve(geom: Geometry, tau: float, u0: float, max_steps: int,
 def adr_params(nspecies: int, tau, c_in=(1.0, 0.0, 0.0),
                precision: int = LBM_F64, max_steps: int = 0, tol: float = 0.0,
                check_every: int = 100, x_plane: int = -1,
-               flags: int = 0, neg_tol: float = 0.0) -> lbm_adr_params:
+               flags: int = 0, neg_tol: float = 0.0,
+               eps_tol: float = 0.0) -> lbm_adr_params:
     """ADR settings; neg_tol 0 keeps the library's default (LBM_EUNSTABLE
     below -0.1 max(1, c_in)), < 0 turns the negative-concentration test
-    off."""
+    off; eps_tol > 0 adds the efficiency test to the steady-state
+    criterion of lbm_adr_solve and Batch.solve (see include/lbm.h)."""
     taus = list(tau) if hasattr(tau, "__len__") else [tau] * nspecies
     taus = (taus + [1.0] * 3)[:3]
     cin = (list(c_in) + [0.0] * 3)[:3]
     return lbm_adr_params(nspecies, precision, (ctypes.c_double * 3)(*taus),
                           (ctypes.c_double * 3)(*cin), int(max_steps), tol,
-                          int(check_every), x_plane, flags, float(neg_tol))
+                          int(check_every), x_plane, flags, float(neg_tol),
+                          float(eps_tol))
 
 
 class ADRSolver:

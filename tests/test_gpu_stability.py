@@ -112,3 +112,40 @@ def test_bounded_undershoot_is_reported(lattice):
     off = _gpu_chunks(lattice, 400, 1, 12, neg_tol=-1.0)
     assert all(s == lbm.LBM_OK for s, _ in off) and len(off) == 12
     assert min(off[-1][1]["c_min"]) < -0.1
+
+
+def test_efficiency_convergence_test():
+    """eps_tol (lbm_adr_solve and the batch): on a diffusion-dominated
+    cascade lattice (Pe = 1, tau_c = 1.7), where a per-step residual of
+    1e-6 is reached long before the efficiency settles, adding the
+    efficiency test (Aitken extrapolation of the last three checks) lands
+    within a few eps_tol of the FP64 steady value (residual 1e-12), in the
+    single solve and in the batch alike."""
+    w = inputs.two_membrane_cascade(seed=3, pe=1.0, nx=512, ny=96,
+                                    bands=((100, 180), (250, 330)),
+                                    per_band=6)
+    geom = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
+    u, fi = lbm.lbm_flow_solve(geom, w.tau_flow, w.u0, 400000, tol=1e-10,
+                               check_every=1000, precision=lbm.LBM_F64)
+    assert fi["converged"]
+
+    def solve(tol, eps_tol, prec=lbm.LBM_F64):
+        prm = lbm.adr_params(3, w.tau_c, precision=prec, max_steps=2000000,
+                             tol=tol, eps_tol=eps_tol, check_every=1000)
+        return lbm.lbm_adr_solve(geom, prm, u if prec == lbm.LBM_F64
+                                 else u.float(), want_conc=False)[1]
+
+    ref = solve(1e-12, 0.0)
+    assert ref["converged"] and ref["eps"] > 1e-3
+    loose = solve(1e-6, 0.0)
+    tight = solve(1e-6, 1e-6)
+    assert tight["converged"] and tight["steps"] >= loose["steps"]
+    assert abs(tight["eps"] - ref["eps"]) < 5e-6, (ref, loose, tight)
+    assert abs(tight["eps"] - ref["eps"]) <= abs(loose["eps"] - ref["eps"])
+    b = lbm.Batch([geom], [lbm.adr_params(3, w.tau_c, precision=lbm.LBM_F32,
+                                          max_steps=2000000, tol=1e-6,
+                                          eps_tol=1e-5, check_every=1000)],
+                  [u.float()])
+    info = b.solve()[0]
+    assert info["converged"]
+    assert abs(info["eps"] - ref["eps"]) < 5e-5, (ref, info)
