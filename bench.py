@@ -15,9 +15,15 @@ The line is the --precision run (FP32 by default).  On one GPU it also
 carries, unless --no-extra: the other two precisions timed the same way
 (fewer steps; their own roofline and clocks; the FP64 step's roofline is
 its FP64 arithmetic against the FMA rate measured on the same GPU by
-lbm_fp64_fma_tflops), and an efficiency check at equal step counts: FP32
-and FP16 storage against FP64 on the full lattice, outfluxes on a plane
-through the middle of the first (A->B) membrane.
+lbm_fp64_fma_tflops); an efficiency check at equal step counts, FP32 and
+FP16 storage against FP64 on the full lattice (outfluxes on the first
+fiber-free plane behind the first (A->B) membrane, and the share of B in the
+lattice); and a steady-state check of the outlet efficiency of Eq. (A-B) on
+the two-membrane cascade lattice (2048 x 512, Da = 1, Pe = 10): FP64 to a
+per-step residual of 1e-9, FP32 to 1e-6, and FP32 and FP16 storage at
+FP64's step count.  On the full lattice the C front needs of order 10^5
+steps to reach the second membrane, far beyond the bench's time, so the
+cascade's non-zero efficiency is checked on the smaller lattice.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f16dev|f64]
 python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
@@ -28,6 +34,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -98,6 +105,9 @@ def _args():
                     help="adjoint-check: steps of each perturbed solve "
                          "after the base state")
     ap.add_argument("--cascade-pe", default="1,10,100")
+    ap.add_argument("--cascade-check-pe", type=float, default=10.0,
+                    help="Pe of the two-membrane cascade steady-state check "
+                         "in the default line (0: left out)")
     ap.add_argument("--cascade-max-steps", type=int, default=3000000)
     return ap.parse_args()
 
@@ -456,10 +466,11 @@ def _measure(precision, geom, w, u, steps, warmup, dev, world, fp64_peak):
 def _eps_check(geom, w, u64, steps, plane, dev):
     """FP32 and FP16 storage against FP64 on the full lattice at equal step
     counts from the same start on the same FP64 flow: outfluxes on a plane
-    through the first (A->B) membrane, where B is made.  Reports
-    each precision's fluxes, the A->B efficiency N_B / (N_A + N_B) on that
-    plane, the cascade efficiency of Eq. (A-B) (N_C / sum N) and the
-    differences to FP64."""
+    just behind the first (A->B) membrane, and the lattice's amount of each
+    species.  Reports each precision's fluxes, the A->B efficiency
+    N_B / (N_A + N_B) on that plane, the cascade efficiency of Eq. (A-B)
+    (N_C / sum N), the share of B in the lattice's species (the conversion
+    so far) and the differences to FP64."""
     import torch
 
     from paper_2109_04455_gb300 import lbm
@@ -473,14 +484,17 @@ def _eps_check(geom, w, u64, steps, plane, dev):
         _, info = lbm.lbm_adr_solve(geom, prm, u64 if name == "f64"
                                     else u64.float(), want_conc=False)
         torch.cuda.empty_cache()
-        f = info["flux"]
+        f, m = info["flux"], info["mass"]
         rec = {"flux": f, "eps_ab": f[1] / (f[0] + f[1]),
-               "eps": info["eps"], "c_min": info["c_min"]}
+               "eps": info["eps"], "c_min": info["c_min"], "mass": m,
+               "conversion_b": m[1] / sum(m)}
         if ref is None:
             ref = rec
         else:
             rec["eps_ab_err_vs_f64"] = abs(rec["eps_ab"] - ref["eps_ab"])
             rec["eps_err_vs_f64"] = abs(rec["eps"] - ref["eps"])
+            rec["conversion_b_err_vs_f64"] = abs(rec["conversion_b"]
+                                                 - ref["conversion_b"])
             rec["flux_rel_err_vs_f64"] = max(
                 abs(a - b) / abs(ref["flux"][0]) for a, b in zip(f, ref["flux"]))
         out[name] = rec
@@ -554,7 +568,7 @@ def run_gpu(a):
 
     # ---- the other precisions (timed the same way, fewer steps) and the
     # efficiency check at equal step counts (one GPU only)
-    others, eps_check = {}, None
+    others, eps_check, cascade = {}, None, None
     if world == 1 and not a.no_extra:
         for name in ("f32", "f16dev", "f64"):
             if name == a.precision:
@@ -565,11 +579,13 @@ def run_gpu(a):
             del sv
             torch.cuda.empty_cache()
             others[name] = rec
-        # the middle of the first (A->B) membrane: B is made there from the
-        # first step (at Da = 0.5 the rate is 6e-5 per step, and B made in
-        # the band has not crossed a plane behind it within these steps)
-        plane = int(round(1.5 * w.nx / 9.0))
+        # the first fiber-free column behind the first (A->B) membrane
+        # (fiber surfaces end at x = 2 W / 9): B made by the band's last
+        # fibers crosses it within these steps
+        plane = int(math.ceil(2.0 * w.nx / 9.0)) + 1
         eps_check = _eps_check(geom, w, u64, a.eps_steps, plane, dev)
+        if a.cascade_check_pe > 0:
+            cascade = cascade_rows([a.cascade_check_pe], a.cascade_max_steps)
 
     if rank == 0:
         line = {
@@ -594,6 +610,8 @@ def run_gpu(a):
             line["other_precisions"] = others
         if eps_check:
             line["eps_check"] = eps_check
+        if cascade:
+            line["cascade_check"] = cascade
         if not a.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
@@ -935,20 +953,26 @@ def run_series(a):
 # ---------------------------------------------------------------------------
 def run_cascade(a):
     """Two-membrane cascade lattice (2048 x 512, 40 + 40 R = 8 fibers,
-    seed 0), Da1 = Da2 = 1, per Pe: FP64 ADR to a per-step residual of 1e-9
-    and FP32 to 1e-6 (checked every 1000 steps); then FP32 and
-    FP16-deviation storage run exactly FP64's step count, so that their
+    seed 0), Da1 = Da2 = 1, per Pe of --cascade-pe (see cascade_rows)."""
+    import torch
+    torch.cuda.set_device(0)
+    cascade_rows([float(v) for v in a.cascade_pe.split(",")],
+                 a.cascade_max_steps, verbose=True)
+
+
+def cascade_rows(pes, max_steps, verbose=False):
+    """The two-membrane cascade lattice per Pe: FP64 ADR to a per-step
+    residual of 1e-9 and FP32 to 1e-6 (checked every 1000 steps); then FP32
+    and FP16-deviation storage run exactly FP64's step count, so that their
     efficiencies are compared with FP64's at equal steps.  Untimed: the
     FP64 flow to a per-step residual of 1e-9 (shared by every Pe, since u0
     is fixed and Pe only sets D).  Timed with CUDA events: each solve.
-    Reports per Pe and precision the steps, seconds, the outlet efficiency
+    Returns per Pe and precision the steps, seconds, the outlet efficiency
     of Eq. (A-B) on x = nx - 3, its difference to FP64, the outflux shares
     and the most negative concentration met at the last check."""
     import torch
 
     from paper_2109_04455_gb300 import inputs, lbm
-    torch.cuda.set_device(0)
-    pes = [float(v) for v in a.cascade_pe.split(",")]
     w0 = inputs.two_membrane_cascade(seed=0, pe=pes[0])
     geom = lbm.Geometry(w0.nx, w0.ny, w0.fibers, w0.k1, w0.k2)
     geom.upload()
@@ -995,9 +1019,9 @@ def run_cascade(a):
     for pe in pes:
         w = inputs.two_membrane_cascade(seed=0, pe=pe)
         row = {"pe": pe, "tau_c": w.tau_c, "k1": w.k1, "k2": w.k2}
-        r64 = solve(w, lbm.LBM_F64, 1e-9, a.cascade_max_steps)
+        r64 = solve(w, lbm.LBM_F64, 1e-9, max_steps)
         row["f64_to_1e-9"] = r64
-        row["f32_to_1e-6"] = solve(w, lbm.LBM_F32, 1e-6, a.cascade_max_steps)
+        row["f32_to_1e-6"] = solve(w, lbm.LBM_F32, 1e-6, max_steps)
         if r64["steps"]:
             for name, prec in (("f32_equal_steps", lbm.LBM_F32),
                                ("f16dev_equal_steps", lbm.LBM_F16DEV)):
@@ -1006,8 +1030,11 @@ def run_cascade(a):
                 if row[k]["eps"] is not None and r64["eps"] is not None:
                     row[k]["eps_err_vs_f64"] = abs(row[k]["eps"] - r64["eps"])
         out["runs"].append(row)
-        print(json.dumps(row), flush=True)
-    print(json.dumps(out), flush=True)
+        if verbose:
+            print(json.dumps(row), flush=True)
+    if verbose:
+        print(json.dumps(out), flush=True)
+    return out
 
 
 # ---------------------------------------------------------------------------
