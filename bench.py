@@ -104,6 +104,12 @@ def _args():
     ap.add_argument("--fd-steps", type=int, default=150000,
                     help="adjoint-check: steps of each perturbed solve "
                          "after the base state")
+    ap.add_argument("--fd-every", type=int, default=0,
+                    help="adjoint-check: record the difference quotient "
+                         "every this many steps (0: only at the end)")
+    ap.add_argument("--fd-fibers", default="",
+                    help="adjoint-check: comma-separated fiber indices "
+                         "instead of 16 random ones")
     ap.add_argument("--cascade-pe", default="1,10,100")
     ap.add_argument("--cascade-check-pe", type=float, default=10.0,
                     help="Pe of the two-membrane cascade steady-state check "
@@ -1122,7 +1128,11 @@ def run_adjoint_check(a):
     dw32 = dw32.cpu().numpy()
     rng = np.random.default_rng(4)
     pick = rng.choice(nf, 16, replace=False)
+    if a.fd_fibers:
+        pick = [int(v) for v in a.fd_fibers.split(",")]
     h = 1e-4
+    every = a.fd_every if a.fd_every > 0 else a.fd_steps
+    marks = list(range(every, a.fd_steps + 1, every))
     rows = []
     for f in pick:
         e = []
@@ -1131,13 +1141,28 @@ def run_adjoint_check(a):
             fb[f, 5] += sgn * h
             gg, sp = solver(fb, lbm.LBM_F64, u)
             sp.state_load(base)
-            info = sp.run(a.fd_steps)
-            e.append(info["eps"])
+            seq, done = [], 0
+            for m in marks:
+                seq.append(sp.run(m - done)["eps"])
+                done = m
+            e.append(seq)
             sp.close()
-        fd = (e[0] - e[1]) / (2 * h)
+        # the difference quotient after each mark of steps past the base
+        # state, and Aitken's extrapolation of its last three values (the
+        # limit of a sequence that approaches it geometrically)
+        q = [(p_ - m_) / (2 * h) for p_, m_ in zip(e[0], e[1])]
+        fd = q[-1]
+        fd_lim = None
+        if len(q) >= 3:
+            d1, d2 = q[-1] - q[-2], q[-2] - q[-3]
+            fd_lim = q[-1] - d1 * d1 / (d1 - d2) if d1 != d2 else q[-1]
         rows.append({"fiber": int(f), "cat": int(fib[f, 3]), "fd": fd,
+                     "fd_by_steps": dict(zip(marks, q)), "fd_aitken": fd_lim,
                      "adjoint_f64": float(dw[f]), "adjoint_f32": float(dw32[f]),
                      "rel_f64_vs_fd": (float(dw[f]) - fd) / fd,
+                     "rel_f64_vs_fd_aitken": (None if fd_lim is None else
+                                              (float(dw[f]) - fd_lim) / fd_lim),
+                     "rel_f32_vs_fd": (float(dw32[f]) - fd) / fd,
                      "rel_f32_vs_f64": (float(dw32[f]) - float(dw[f]))
                      / float(dw[f])})
         print(json.dumps(rows[-1]), flush=True)
@@ -1151,6 +1176,7 @@ def run_adjoint_check(a):
                                    np.linalg.norm(dw)),
         "h": h, "fd_steps": a.fd_steps,
         "max_rel_f64_vs_fd": max(abs(r["rel_f64_vs_fd"]) for r in rows),
+        "max_rel_f32_vs_fd": max(abs(r["rel_f32_vs_fd"]) for r in rows),
         "max_rel_f32_vs_f64": max(abs(r["rel_f32_vs_f64"]) for r in rows),
         "seconds": time.perf_counter() - t_all, "rows": rows}), flush=True)
 

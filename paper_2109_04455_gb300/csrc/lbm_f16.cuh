@@ -128,6 +128,9 @@ __device__ __forceinline__ float2 push2(int i, float2 g, float2 e, const PushK2 
 #ifndef LBM_F16_SR
 #define LBM_F16_SR 1
 #endif
+#ifndef LBM_PAIR_PER_SPECIES
+#define LBM_PAIR_PER_SPECIES 0
+#endif
 // Hash of (node pair, step) for the random bits.  Its constants are
 // published integer-hash multipliers: 0x9E3779B1 (2^32 divided by the golden
 // ratio, Knuth's multiplicative hashing), 0x85EBCA77 (the second 32-bit
@@ -377,6 +380,8 @@ template <int NS, int MODE>
 __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
     adr_bulk_pair_kernel(const AdrArgs a) {
   const int y = blockIdx.y;
+  if (LBM_PREFETCH_ROWS_F16 > 0)
+    bulk_prefetch_rows<__half, float, NS, true>(a, y + LBM_PREFETCH_ROWS_F16);
   const int x0 = 2 * (blockIdx.x * kPairThreads + threadIdx.x);
   const long long n0 = (long long)y * a.nx_pad + x0;
   uint2 lw = make_uint2(kSolidNode, kSolidNode);
@@ -387,6 +392,14 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
   for (int k = 0; k < 3 * NS; ++k) acc[0][k] = acc[1][k] = 0.0f;
   if (in0 || in1) {
     const __half2 z2 = __float2half2_rn(0.0f);
+#if LBM_PAIR_PER_SPECIES
+    // each species' pairs are loaded as its arithmetic needs them (the
+    // stores of one species keep the next one's loads behind them)
+    pair_update<NS, MODE>(a, y, x0, in0, in1, [&](int s, int k) {
+      const PairSrc q = pair_src(a, s, k, y, x0, in0, in1);
+      return q.need ? *reinterpret_cast<const __half2 *>(q.p) : z2;
+    }, acc);
+#else
     __half2 v[NS][kPairSlots];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -398,6 +411,7 @@ __global__ void __launch_bounds__(kPairThreads, LBM_PAIR_MIN_BLOCKS)
     }
     pair_update<NS, MODE>(a, y, x0, in0, in1,
                           [&](int s, int k) { return v[s][k]; }, acc);
+#endif
   }
   if constexpr (MODE == kAdrCheck) {
     const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "lbm_internal.h"
 
@@ -516,6 +517,57 @@ __device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
   }
 }
 
+// L2 prefetch ahead of the bulk stencil.  With D = LBM_PREFETCH_ROWS_* > 0
+// each block of the bulk step asks L2 for the row segments that the block D
+// rows further down will read: one bulk prefetch per plane (the 9 NS
+// population rows y + D - c_iy, for FP16 storage the NS reference rows, u
+// and the link words of row y + D).  Blocks start in row order, so those
+// lines are on their way from HBM about D rows of blocks before their loads
+// are issued, and they are in flight without holding registers.
+#ifndef LBM_PREFETCH_ROWS_F16
+#define LBM_PREFETCH_ROWS_F16 6
+#endif
+#ifndef LBM_PREFETCH_ROWS_F32
+#define LBM_PREFETCH_ROWS_F32 0
+#endif
+// [p, p + bytes) into L2, nothing to wait for; p 16-byte aligned and bytes
+// a multiple of 16
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+               :: "l"(p), "r"(bytes) : "memory");
+}
+// S: stored population type, U: velocity type, REF: reference planes
+// (FP16 storage).  Rows outside the lattice are skipped.
+template <typename S, typename U, int NS, bool REF>
+__device__ __forceinline__ void bulk_prefetch_rows(const AdrArgs &a, int yp) {
+  constexpr int kPop = 9 * NS, kRef = REF ? NS : 0;
+  const int t = threadIdx.x;
+  if (t >= kPop + kRef + 3 || yp >= a.ny) return;
+  const long long np = a.nx_pad, plane = a.plane;
+  const int xb = blockIdx.x * kBlockX;
+  // nx_pad is a multiple of 32 and xb of kBlockX, so every segment starts
+  // 64-byte aligned (buffers are 256-byte aligned) and is a multiple of 64
+  // bytes long
+  const unsigned cnt = static_cast<unsigned>(min(kBlockX, a.nx_pad - xb));
+  if (t < kPop) {
+    const int i = t % 9, row = yp - cy(i);
+    if (row < 0 || row >= a.ny) return;
+    prefetch_l2(static_cast<const S *>(a.src) + (long long)t * plane +
+                    (long long)row * np + xb,
+                static_cast<unsigned>(sizeof(S)) * cnt);
+  } else if (t < kPop + kRef) {
+    prefetch_l2(a.rsrc + (long long)(t - kPop) * plane + (long long)yp * np + xb,
+                static_cast<unsigned>(sizeof(RefT)) * cnt);
+  } else if (t < kPop + kRef + 2) {
+    prefetch_l2(static_cast<const U *>(a.u) + (long long)(t - kPop - kRef) * plane +
+                    (long long)yp * np + xb,
+                static_cast<unsigned>(sizeof(U)) * cnt);
+  } else {
+    prefetch_l2(a.links + (long long)yp * np + xb, 4u * cnt);
+  }
+}
+
+
 }  // namespace lbm
 // FP16-deviation storage: interior update (one and two nodes per thread)
 #include "lbm_f16.cuh"
@@ -612,6 +664,8 @@ template <class P, int NS, int MODE>
 __global__ void __launch_bounds__(kBlockX, LBM_MIN_BLOCKS(P))
     adr_bulk_kernel(const AdrArgs a) {
   using T = typename P::T;
+  if constexpr (std::is_same<typename P::S, float>::value && LBM_PREFETCH_ROWS_F32 > 0)
+    bulk_prefetch_rows<float, float, NS, false>(a, blockIdx.y + LBM_PREFETCH_ROWS_F32);
   const int x = blockIdx.x * kBlockX + threadIdx.x;
   const long long n = (long long)blockIdx.y * a.nx_pad + x;
   const uint32_t lw = (x < a.nx_pad) ? a.links[n] : kSolidNode;
