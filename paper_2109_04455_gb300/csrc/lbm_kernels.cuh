@@ -38,8 +38,11 @@ namespace lbm {
 #ifndef LBM_ADR_PAIR_F16
 #define LBM_ADR_PAIR_F16 1
 #endif
+//   LBM_PAIR_MIN_BLOCKS resident blocks per SM asked of the register
+//                      allocator for adr_bulk_pair_kernel (6: 80 registers
+//                      with per-species loads)
 #ifndef LBM_PAIR_MIN_BLOCKS
-#define LBM_PAIR_MIN_BLOCKS 4
+#define LBM_PAIR_MIN_BLOCKS 6
 #endif
 constexpr int kBlockX = LBM_BLOCK_X;
 #ifdef LBM_ADR_MIN_BLOCKS
