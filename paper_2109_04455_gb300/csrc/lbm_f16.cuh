@@ -295,7 +295,8 @@ __device__ __forceinline__ PairSrc pair_src(const AdrArgs &a, int s, int k,
 // the recorded concentrations, and adds the check-step values to acc.
 template <int NS, int MODE, class Fetch>
 __device__ __forceinline__ void pair_update(const AdrArgs &a, int y, int x0,
-                                            bool in0, bool in1, Fetch &&fetch,
+                                            bool in0, bool in1, float2 ux,
+                                            float2 uy, Fetch &&fetch,
                                             float (&acc)[2][3 * NS]) {
   const long long np = a.nx_pad, plane = a.plane;
   const long long n0 = (long long)y * np + x0;
@@ -307,9 +308,6 @@ __device__ __forceinline__ void pair_update(const AdrArgs &a, int y, int x0,
     for (int s = 0; s < NS; ++s)
       prev[s] = *reinterpret_cast<const float2 *>(cp + s * plane + n0);
   }
-  const float *__restrict__ U = static_cast<const float *>(a.u);
-  const float2 ux = *reinterpret_cast<const float2 *>(U + n0);
-  const float2 uy = *reinterpret_cast<const float2 *>(U + plane + n0);
   float2 E[9];
   f16::eq2(ux, uy, E);
   const uint32_t hp = f16::pair_hash(n0 >> 1, a.step);
@@ -398,10 +396,13 @@ __global__ void __launch_bounds__(kPairThreads, MODE == kAdrCheck ? 5 : LBM_PAIR
   for (int k = 0; k < 3 * NS; ++k) acc[0][k] = acc[1][k] = 0.0f;
   if (in0 || in1) {
     const __half2 z2 = __float2half2_rn(0.0f);
+    const float *__restrict__ U = static_cast<const float *>(a.u);
+    const float2 ux = *reinterpret_cast<const float2 *>(U + n0);
+    const float2 uy = *reinterpret_cast<const float2 *>(U + a.plane + n0);
 #if LBM_PAIR_PER_SPECIES
     // each species' pairs are loaded as its arithmetic needs them (the
     // stores of one species keep the next one's loads behind them)
-    pair_update<NS, MODE>(a, y, x0, in0, in1, [&](int s, int k) {
+    pair_update<NS, MODE>(a, y, x0, in0, in1, ux, uy, [&](int s, int k) {
       const PairSrc q = pair_src(a, s, k, y, x0, in0, in1);
       return q.need ? *reinterpret_cast<const __half2 *>(q.p) : z2;
     }, acc);
@@ -415,7 +416,7 @@ __global__ void __launch_bounds__(kPairThreads, MODE == kAdrCheck ? 5 : LBM_PAIR
         v[s][k] = q.need ? *reinterpret_cast<const __half2 *>(q.p) : z2;
       }
     }
-    pair_update<NS, MODE>(a, y, x0, in0, in1,
+    pair_update<NS, MODE>(a, y, x0, in0, in1, ux, uy,
                           [&](int s, int k) { return v[s][k]; }, acc);
 #endif
   }
