@@ -23,7 +23,11 @@ the two-membrane cascade lattice (2048 x 512, Da = 1, Pe = 10): FP64 to a
 per-step residual of 1e-9, FP32 to 1e-6, and FP32 and FP16 storage at
 FP64's step count.  On the full lattice the C front needs of order 10^5
 steps to reach the second membrane, far beyond the bench's time, so the
-cascade's non-zero efficiency is checked on the smaller lattice.
+cascade's non-zero efficiency is checked on the smaller lattice.  Last, the
+Pe x Da sweep record: the 64-instance sweep (61 with k < 1), every instance
+2000 steps in every precision, one lbm_adr_solve per instance in FP64 and
+FP32 against one batch in FP32 and FP16 storage (solves/s and the largest
+efficiency difference to FP64 at equal step counts).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f32|f16dev|f64]
 python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
@@ -111,6 +115,9 @@ def _args():
                     help="adjoint-check: comma-separated fiber indices "
                          "instead of 16 random ones")
     ap.add_argument("--cascade-pe", default="1,10,100")
+    ap.add_argument("--sweep-check-steps", type=int, default=2000,
+                    help="steps per instance of the Pe x Da sweep record in "
+                         "the default line (0: left out)")
     ap.add_argument("--cascade-check-pe", type=float, default=10.0,
                     help="Pe of the two-membrane cascade steady-state check "
                          "in the default line (0: left out)")
@@ -579,7 +586,7 @@ def run_gpu(a):
 
     # ---- the other precisions (timed the same way, fewer steps) and the
     # efficiency check at equal step counts (one GPU only)
-    others, eps_check, cascade = {}, None, None
+    others, eps_check, cascade, sweep = {}, None, None, None
     if world == 1 and not a.no_extra:
         for name in ("f32", "f16dev", "f64"):
             if name == a.precision:
@@ -597,6 +604,9 @@ def run_gpu(a):
         eps_check = _eps_check(geom, w, u64, a.eps_steps, plane, dev)
         if a.cascade_check_pe > 0:
             cascade = cascade_rows([a.cascade_check_pe], a.cascade_max_steps)
+        if a.sweep_check_steps > 0:
+            sweep = sweep_record(a.sweep_instances, a.sweep_check_steps,
+                                 a.sweep_flow_steps, 0.0)
 
     if rank == 0:
         line = {
@@ -625,6 +635,8 @@ def run_gpu(a):
             line["eps_check"] = eps_check
         if cascade:
             line["cascade_check"] = cascade
+        if sweep:
+            line["sweep"] = sweep
         if not a.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
@@ -681,14 +693,20 @@ def run_sweep_steady(a):
         torch.cuda.synchronize()
         return out, ev0.elapsed_time(ev1) * 1e-3
 
+    def one(g, p, u):
+        # a lattice that goes unstable is reported in its row, not raised
+        try:
+            return lbm.lbm_adr_solve(g, p, u, want_conc=False)[1]
+        except lbm.LBMError as e:
+            return {"eps": float("nan"), "steps": p.max_steps,
+                    "converged": 0, "status": str(e)}
+
     res = {}
-    ref, t64 = timed(lambda: [lbm.lbm_adr_solve(g, p, u, want_conc=False)[1]
-                              for g, p, u in zip(geoms, params(
-                                  lbm.LBM_F64, 1e-9, 1e-7), u64)])
+    ref, t64 = timed(lambda: [one(g, p, u) for g, p, u in zip(
+        geoms, params(lbm.LBM_F64, 1e-9, 1e-7), u64)])
     res["f64_unbatched"] = (ref, t64)
-    r32, t32 = timed(lambda: [lbm.lbm_adr_solve(g, p, u, want_conc=False)[1]
-                              for g, p, u in zip(geoms, params(
-                                  lbm.LBM_F32, 1e-6, 1e-5), u32)])
+    r32, t32 = timed(lambda: [one(g, p, u) for g, p, u in zip(
+        geoms, params(lbm.LBM_F32, 1e-6, 1e-5), u32)])
     res["f32_unbatched"] = (r32, t32)
     for name, prec, tol in (("f32_batched", lbm.LBM_F32, 1e-6),
                             ("f16dev_batched", lbm.LBM_F16DEV, 1e-5)):
@@ -704,12 +722,14 @@ def run_sweep_steady(a):
            "check_every": check, "flow": {"steps": flow_steps,
                                           "seconds_untimed": flow_s}}
     for name, (infos, t) in res.items():
-        errs = [abs(i["eps"] - r["eps"]) for i, r in zip(infos, ref)]
+        errs = [abs(i["eps"] - r["eps"]) for i, r in zip(infos, ref)
+                if math.isfinite(i["eps"]) and math.isfinite(r["eps"])]
         out[name] = {"solves_per_s": len(ws) / t, "seconds": t,
                      "speedup_vs_f64": t64 / t,
                      "converged": sum(bool(i["converged"]) for i in infos),
                      "steps": sum(i["steps"] for i in infos),
-                     "max_abs_eps_err_vs_f64": max(errs),
+                     "max_abs_eps_err_vs_f64": max(errs) if errs else None,
+                     "instances_compared": len(errs),
                      "instances_over_1e-3": sum(e > 1e-3 for e in errs)}
     out["per_instance"] = [
         {"pe": round(w.pe, 4), "da": round(w.da1, 4), "nx": w.nx, "ny": w.ny,
@@ -723,35 +743,43 @@ def run_sweep_steady(a):
 
 
 def run_sweep(a):
-    """64 seeded lattices (Pe = logspace(-1,2,8) x Da = logspace(-2,2,8),
-    widths 512..2048, heights 256..512), each with its own flow (FP64, fixed
-    step count, untimed).  Timed: the ADR solves of all instances to their
-    step count (default: every instance runs exactly --sweep-max-steps
-    steps in every precision, so the efficiencies are compared at equal
-    step counts; a per-step residual of 1e-6 is no steady state on these
-    lattices, and stopping there leaves the efficiency off by up to 1e-2),
-    or with --sweep-tol to a residual tolerance;
-    batched (one lbm_batch for all, FP32 and FP16 storage) against one
-    lbm_adr_solve per instance in FP64 and in FP32.  Reports solves/s and the largest
-    efficiency difference to FP64."""
+    """The Pe x Da sweep at fixed step counts (see sweep_record)."""
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps(sweep_record(a.sweep_instances, a.sweep_max_steps,
+                                  a.sweep_flow_steps, a.sweep_tol)), flush=True)
+
+
+def sweep_record(n_instances, max_steps, flow_steps, sweep_tol):
+    """The first n_instances seeded lattices of the sweep (Pe =
+    logspace(-1,2,8) x Da = logspace(-2,2,8), widths 512..2048, heights
+    256..512), each with its own flow (FP64, flow_steps steps, untimed).
+    Timed: the ADR solves of all instances.  sweep_tol <= 0: every instance
+    runs exactly max_steps steps in every precision, so the efficiencies
+    are compared at equal step counts (a per-step residual of 1e-6 is no
+    steady state on these lattices, and stopping there leaves the
+    efficiency off by up to 1e-2); otherwise each solve stops at that
+    residual (FP64 at 1e-3 of it).  Batched (one lbm_batch for all, FP32
+    and FP16 storage) against one lbm_adr_solve per instance in FP64 and in
+    FP32.  Returns solves/s and the largest efficiency difference to
+    FP64."""
     import torch
 
     from paper_2109_04455_gb300 import inputs, lbm
-    torch.cuda.set_device(0)
-    ws_all = [inputs.sweep_instance(i) for i in range(a.sweep_instances)]
+    ws_all = [inputs.sweep_instance(i) for i in range(n_instances)]
     # the explicit Dawson source needs k < 1 per step (k = 1 empties A in one
     # step); the (Pe, Da) pairs with k = Da D / R^2 >= 1 are left out
     ws = [w for w in ws_all if max(w.k1, w.k2) < 1.0]
     geoms, u64 = [], []
     for w in ws:
         g = lbm.Geometry(w.nx, w.ny, w.fibers, w.k1, w.k2).upload()
-        u, _ = lbm.lbm_flow_solve(g, w.tau_flow, w.u0, a.sweep_flow_steps,
+        u, _ = lbm.lbm_flow_solve(g, w.tau_flow, w.u0, flow_steps,
                                   precision=lbm.LBM_F64)
         geoms.append(g)
         u64.append(u)
     nodes = sum(w.nx * w.ny for w in ws)
     check = 500
-    cap = a.sweep_max_steps
+    cap = max_steps
 
     def params(prec, tol):
         return [lbm.adr_params(3, w.tau_c, precision=prec, max_steps=cap,
@@ -760,7 +788,7 @@ def run_sweep(a):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(
         enable_timing=True)
     # unbatched FP64
-    p64 = params(lbm.LBM_F64, a.sweep_tol * 1e-3)
+    p64 = params(lbm.LBM_F64, sweep_tol * 1e-3)
     torch.cuda.synchronize()
     ev0.record()
     ref = [lbm.lbm_adr_solve(g, p, u, want_conc=False)[1]
@@ -769,8 +797,8 @@ def run_sweep(a):
     torch.cuda.synchronize()
     t64 = ev0.elapsed_time(ev1) * 1e-3
     out = {"metric": "Pe x Da sweep solves/s (ADR, 3 species)",
-           "mode": ("fixed step count" if a.sweep_tol <= 0 else
-                    f"to a residual of {a.sweep_tol:g}"),
+           "mode": ("fixed step count" if sweep_tol <= 0 else
+                    f"to a residual of {sweep_tol:g}"),
            "unit": "solves/s", "higher_is_better": True,
            "instances": len(ws),
            "left_out_k_ge_1": len(ws_all) - len(ws),
@@ -781,7 +809,7 @@ def run_sweep(a):
                              "steps": sum(r["steps"] for r in ref)}}
     u32 = [u.float() for u in u64]
     # unbatched FP32: the gain of batching alone, at the same precision
-    p32 = params(lbm.LBM_F32, a.sweep_tol)
+    p32 = params(lbm.LBM_F32, sweep_tol)
     torch.cuda.synchronize()
     ev0.record()
     ref32 = [lbm.lbm_adr_solve(g, p, u, want_conc=False)[1]
@@ -794,8 +822,8 @@ def run_sweep(a):
                             "steps": sum(r["steps"] for r in ref32)}
     # with a tolerance: FP64 to tol * 1e-3, FP32 to tol, FP16 (stochastic
     # rounding: a per-step residual floor of a few 1e-6) to max(tol, 1e-5)
-    tols = {lbm.LBM_F32: a.sweep_tol,
-            lbm.LBM_F16DEV: max(a.sweep_tol, 1e-5) if a.sweep_tol > 0 else 0.0}
+    tols = {lbm.LBM_F32: sweep_tol,
+            lbm.LBM_F16DEV: max(sweep_tol, 1e-5) if sweep_tol > 0 else 0.0}
     for name, prec in (("f32_batched", lbm.LBM_F32),
                        ("f16dev_batched", lbm.LBM_F16DEV)):
         tol = tols[prec]
@@ -816,7 +844,10 @@ def run_sweep(a):
                      "steps": sum(i["steps"] for i in infos),
                      "tile": tile, "grid": grid}
         b.close()
-    print(json.dumps(out), flush=True)
+    for g in geoms:
+        g.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
