@@ -705,8 +705,12 @@ def run_sweep_steady(a):
     ref, t64 = timed(lambda: [one(g, p, u) for g, p, u in zip(
         geoms, params(lbm.LBM_F64, 1e-9, 1e-7), u64)])
     res["f64_unbatched"] = (ref, t64)
+    print(json.dumps({"phase": "f64_unbatched", "seconds": t64,
+                      "flow_seconds_untimed": flow_s,
+                      "steps": sum(r["steps"] for r in ref)}), flush=True)
     r32, t32 = timed(lambda: [one(g, p, u) for g, p, u in zip(
         geoms, params(lbm.LBM_F32, 1e-6, 1e-5), u32)])
+    print(json.dumps({"phase": "f32_unbatched", "seconds": t32}), flush=True)
     res["f32_unbatched"] = (r32, t32)
     for name, prec, tol in (("f32_batched", lbm.LBM_F32, 1e-6),
                             ("f16dev_batched", lbm.LBM_F16DEV, 1e-5)):
