@@ -378,8 +378,12 @@ __device__ __forceinline__ void pair_update(const AdrArgs &a, int y, int x0,
   }
 }
 
-// Register-staged form: the thread loads its 24 x NS pairs into registers,
-// all before any arithmetic (so they are in flight together).
+// The bulk kernel.  A block first sends the L2 prefetches for the block
+// LBM_PREFETCH_ROWS_F16 rows below it, then each thread loads its pairs
+// (per species by default, or all 24 x NS before any arithmetic with
+// LBM_PAIR_PER_SPECIES = 0) and updates its two nodes.  The check-step form
+// keeps its partial sums as well and is bounded at 5 blocks per SM (96
+// registers) so that it does not spill.
 template <int NS, int MODE>
 __global__ void __launch_bounds__(kPairThreads, MODE == kAdrCheck ? 5 : LBM_PAIR_MIN_BLOCKS)
     adr_bulk_pair_kernel(const AdrArgs a) {
