@@ -349,8 +349,8 @@ __device__ __forceinline__ void pair_update(const AdrArgs &a, int y, int x0,
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const float2 v = f16::push2(i, g[i], E[i], kk);
-        bulk_store(reinterpret_cast<__half2 *>(o + (long long)i * plane),
-                   f16::round_pair(v.x, v.y, hp, s * 9 + i));
+        *reinterpret_cast<__half2 *>(o + (long long)i * plane) =
+            f16::round_pair(v.x, v.y, hp, s * 9 + i);
       }
       *reinterpret_cast<__half2 *>(ro) = cr;
       if (MODE == kAdrCheck) *reinterpret_cast<float2 *>(co) = c;

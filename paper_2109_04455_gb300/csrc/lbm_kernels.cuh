@@ -520,21 +520,6 @@ __device__ __forceinline__ void adr_general_node(const AdrArgs &a, long long n,
   }
 }
 
-// Stores of the bulk steps' new populations.  LBM_STREAM_STORES = 1: with
-// the evict-first (streaming) cache hint, so that the written lines do not
-// push the prefetched source rows out of L2 before they are read.
-#ifndef LBM_STREAM_STORES
-#define LBM_STREAM_STORES 0
-#endif
-template <typename S>
-__device__ __forceinline__ void bulk_store(S *p, S v) {
-#if LBM_STREAM_STORES
-  __stcs(p, v);
-#else
-  *p = v;
-#endif
-}
-
 // L2 prefetch ahead of the bulk stencil.  With D = LBM_PREFETCH_ROWS_* > 0
 // each block of the bulk step asks L2 for the row segments that the block D
 // rows further down will read: one bulk prefetch per plane (the 9 NS
@@ -634,8 +619,8 @@ __device__ __forceinline__ void adr_interior_node(const AdrArgs &a, long long n,
     const T om = pick<T>(a.omega[s], a.fomega[s]);
 #pragma unroll
     for (int i = 0; i < 9; ++i)
-      bulk_store(&dst[(long long)(s * 9 + i) * plane + n],
-                 P::store(g[s][i] + om * (c * E[i] - g[s][i])));
+      dst[(long long)(s * 9 + i) * plane + n] =
+          P::store(g[s][i] + om * (c * E[i] - g[s][i]));
     if (MODE == kAdrCheck) {
       check_add<NS, T>(acc, s, c, prev[s]);
       cp[s * plane + n] = c;
