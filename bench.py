@@ -588,25 +588,39 @@ def run_gpu(a):
     # efficiency check at equal step counts (one GPU only)
     others, eps_check, cascade, sweep = {}, None, None, None
     if world == 1 and not a.no_extra:
-        for name in ("f32", "f16dev", "f64"):
-            if name == a.precision:
-                continue
+        # each record is optional: one that fails is reported in its place
+        # (its error text), and the headline record above still prints
+        def guarded(fn):
+            try:
+                return fn()
+            except Exception as e:   # noqa: BLE001 (reported, not hidden)
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
+                return {"error": f"{type(e).__name__}: {e}"}
+
+        def other(name):
             rec, sv, _ = _measure(name, geom, w, vel(name), a.extra_steps, 3,
                                   dev, world, fp64_peak)
             sv.close()
-            del sv
             torch.cuda.empty_cache()
-            others[name] = rec
+            return rec
+
+        for name in ("f32", "f16dev", "f64"):
+            if name != a.precision:
+                others[name] = guarded(lambda: other(name))
         # the first fiber-free column behind the first (A->B) membrane
         # (fiber surfaces end at x = 2 W / 9): B made by the band's last
         # fibers crosses it within these steps
         plane = int(math.ceil(2.0 * w.nx / 9.0)) + 1
-        eps_check = _eps_check(geom, w, u64, a.eps_steps, plane, dev)
+        eps_check = guarded(lambda: _eps_check(geom, w, u64, a.eps_steps,
+                                               plane, dev))
         if a.cascade_check_pe > 0:
-            cascade = cascade_rows([a.cascade_check_pe], a.cascade_max_steps)
+            cascade = guarded(lambda: cascade_rows([a.cascade_check_pe],
+                                                   a.cascade_max_steps))
         if a.sweep_check_steps > 0:
-            sweep = sweep_record(a.sweep_instances, a.sweep_check_steps,
-                                 a.sweep_flow_steps, 0.0)
+            sweep = guarded(lambda: sweep_record(
+                a.sweep_instances, a.sweep_check_steps, a.sweep_flow_steps,
+                0.0))
 
     if rank == 0:
         line = {
