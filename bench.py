@@ -652,7 +652,10 @@ def run_gpu(a):
         if sweep:
             line["sweep"] = sweep
         if not a.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(w)
+            try:
+                line["cpu_baseline"] = cpu_baseline(w)
+            except Exception as e:   # noqa: BLE001 (reported, not hidden)
+                line["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
