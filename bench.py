@@ -95,6 +95,8 @@ def _args():
                          "side-by-side fiber, Da = 150 and 1.5)")
     ap.add_argument("--adjoint-iters", type=int, default=200)
     ap.add_argument("--sweep-instances", type=int, default=64)
+    ap.add_argument("--sweep-first", type=int, default=0,
+                    help="steady sweep: index of the first instance")
     ap.add_argument("--sweep-max-steps", type=int, default=5000)
     ap.add_argument("--sweep-tol", type=float, default=0.0,
                     help="residual tolerance of the sweep solves; 0 (default) "
@@ -678,7 +680,8 @@ def run_sweep_steady(a):
 
     from paper_2109_04455_gb300 import inputs, lbm
     torch.cuda.set_device(0)
-    ws_all = [inputs.sweep_instance(i) for i in range(a.sweep_instances)]
+    ws_all = [inputs.sweep_instance(i) for i in
+              range(a.sweep_first, a.sweep_first + a.sweep_instances)]
     ws = [w for w in ws_all if max(w.k1, w.k2) < 1.0]
     geoms, u64 = [], []
     t0 = time.perf_counter()
