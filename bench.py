@@ -450,7 +450,7 @@ def _measure(precision, geom, w, u, steps, warmup, dev, world, fp64_peak):
     achieved = alg_bytes / step_launch_s / 1e9
     peak, peak_kind = _peak_hbm()
     traffic = _ncu_traffic(precision, n_fluid)
-    kernel = ("adr_bulk_pair_kernel<3 species,step> (f16dev)"
+    kernel = ("adr_bulk_quad_kernel<3 species> (f16dev, plain steps)"
               if precision == "f16dev" else
               f"adr_bulk_kernel<{precision},3 species,step>")
     if precision != "f64":

@@ -431,4 +431,163 @@ __global__ void __launch_bounds__(kPairThreads, MODE == kAdrCheck ? 5 : LBM_PAIR
   }
 }
 
+// FP16 plain step, four nodes per thread: nodes x0 .. x0 + 3 (x0 a multiple
+// of 4) of row y, with every plane read and written as aligned 8-byte
+// quads.  A pull with c_ix = +1 takes the sources x0 - 1 .. x0 + 2: the
+// last half of the quad to the left (one 2-byte load) and three halves of
+// the node's own quad; c_ix = -1 takes x0 + 1 .. x0 + 4, the first half of
+// the quad to the right.  The left half is loaded only when node x0 is
+// interior (then x0 - 1 is a lattice node) and the right one only when node
+// x0 + 3 is (then x0 + 4 <= nx - 1 < nx_pad); rows y +- 1 exist whenever a
+// node of the quad is interior.  The reference concentrations come the same
+// way, three rows of one quad and two single halves per species.  Against
+// the two-node kernel this halves the load instructions and the address
+// arithmetic per node.  The arithmetic is that of pair_update on the pairs
+// (x0, x0 + 1) and (x0 + 2, x0 + 3), operation for operation (the same
+// packed roundings, the same random bits per pair), so every stored half is
+// the two-node kernel's.  Plain steps only: check steps keep the two-node
+// kernel, which also writes the partial sums.  Launched with kBlockX / 4
+// threads on the grid of adr_bulk_kernel.
+#ifndef LBM_QUAD_MIN_BLOCKS
+#define LBM_QUAD_MIN_BLOCKS 8
+#endif
+constexpr int kQuadThreads = kBlockX / 4;
+
+template <int NS>
+__global__ void __launch_bounds__(kQuadThreads, LBM_QUAD_MIN_BLOCKS)
+    adr_bulk_quad_kernel(const AdrArgs a) {
+  static_assert(kQuadThreads >= 9 * NS + NS + 3, "one prefetch per thread");
+  static_assert(kQuadThreads % 32 == 0, "whole warps");
+  const int y = blockIdx.y;
+  if (LBM_PREFETCH_ROWS_F16 > 0)
+    bulk_prefetch_rows<__half, float, NS, true>(a, y + LBM_PREFETCH_ROWS_F16);
+  const int x0 = 4 * (blockIdx.x * kQuadThreads + threadIdx.x);
+  if (x0 >= a.nx_pad) return;   // nx_pad is a multiple of 4: x0 + 3 < nx_pad
+  const long long np = a.nx_pad, plane = a.plane;
+  const long long n0 = (long long)y * np + x0;
+  const uint4 lw = *reinterpret_cast<const uint4 *>(a.links + n0);
+  const bool in0 = lw.x == 0u, in1 = lw.y == 0u, in2 = lw.z == 0u, in3 = lw.w == 0u;
+  if (!(in0 || in1 || in2 || in3)) return;
+  const bool all = in0 && in1 && in2 && in3;
+  const __half *src = static_cast<const __half *>(a.src);
+  __half *__restrict__ dst = static_cast<__half *>(a.dst);
+  const float *__restrict__ U = static_cast<const float *>(a.u);
+  const float4 ux = *reinterpret_cast<const float4 *>(U + n0);
+  const float4 uy = *reinterpret_cast<const float4 *>(U + plane + n0);
+  float2 El[9], Eh[9];
+  f16::eq2(make_float2(ux.x, ux.y), make_float2(uy.x, uy.y), El);
+  f16::eq2(make_float2(ux.z, ux.w), make_float2(uy.z, uy.w), Eh);
+  // random bits of the pairs (x0, x0 + 1) and (x0 + 2, x0 + 3)
+  const uint32_t hl = f16::pair_hash(n0 >> 1, a.step);
+  const uint32_t hh = f16::pair_hash((n0 >> 1) + 1, a.step);
+  const __half hz = __float2half_rn(0.0f);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    // the species' loads, issued before its arithmetic: nine own quads,
+    // six side halves, and per row y - 1 .. y + 1 the reference quad with
+    // its two side halves
+    uint2 q[9];
+    __half side[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const __half *row = src + (long long)(s * 9 + i) * plane +
+                          (long long)(y - cy(i)) * np + x0;
+      q[i] = *reinterpret_cast<const uint2 *>(row);
+      side[i] = hz;
+      if (cx(i) > 0 && in0) side[i] = row[-1];
+      if (cx(i) < 0 && in3) side[i] = row[4];
+    }
+    uint2 rq[3];
+    __half rl[3], rr[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const __half *row = a.rsrc + (long long)s * plane + (long long)(y + r - 1) * np + x0;
+      rq[r] = *reinterpret_cast<const uint2 *>(row);
+      rl[r] = in0 ? row[-1] : hz;
+      rr[r] = in3 ? row[4] : hz;
+    }
+    // reference concentrations of the source columns x0 - 1 .. x0 + 4
+    float rs[3][6];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      __half2 lo, hi;
+      memcpy(&lo, &rq[r].x, 4);
+      memcpy(&hi, &rq[r].y, 4);
+      const float2 fl = __half22float2(lo), fh = __half22float2(hi);
+      rs[r][0] = __half2float(rl[r]);
+      rs[r][1] = fl.x;
+      rs[r][2] = fl.y;
+      rs[r][3] = fh.x;
+      rs[r][4] = fh.y;
+      rs[r][5] = __half2float(rr[r]);
+    }
+    float2 gl[9], gh[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int r = 1 - cy(i);   // source row y - cy(i)
+      const int k = 1 - cx(i);   // column of node x0's source, x0 - 1 + k
+      __half2 lo, hi;
+      memcpy(&lo, &q[i].x, 4);
+      memcpy(&hi, &q[i].y, 4);
+      const float2 fl = __half22float2(lo), fh = __half22float2(hi);
+      const float p[6] = {__half2float(side[i]), fl.x, fl.y, fh.x, fh.y,
+                          __half2float(side[i])};
+      const float2 wk = f16::dup(f16::w(i) * f16::kUp);
+      gl[i] = __ffma2_rn(wk, make_float2(rs[r][k], rs[r][k + 1]),
+                         make_float2(p[k], p[k + 1]));
+      gh[i] = __ffma2_rn(wk, make_float2(rs[r][k + 2], rs[r][k + 3]),
+                         make_float2(p[k + 2], p[k + 3]));
+    }
+    const float2 csl = f16::sum9(gl), csh = f16::sum9(gh);
+    const float2 cl = __fmul2_rn(csl, f16::dup(f16::kDown));
+    const float2 ch = __fmul2_rn(csh, f16::dup(f16::kDown));
+    const __half2 crl = __float22half2_rn(cl), crh = __float22half2_rn(ch);
+    const f16::PushK2 kl = f16::push_k2(
+        a.fomega[s], csl, __fmul2_rn(__half22float2(crl), f16::dup(f16::kUp)));
+    const f16::PushK2 kh = f16::push_k2(
+        a.fomega[s], csh, __fmul2_rn(__half22float2(crh), f16::dup(f16::kUp)));
+    __half *o = dst + (long long)s * 9 * plane + n0;
+    __half *ro = a.rdst + (long long)s * plane + n0;
+    if (all) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const float2 vl = f16::push2(i, gl[i], El[i], kl);
+        const float2 vh = f16::push2(i, gh[i], Eh[i], kh);
+        const __half2 rl2 = f16::round_pair(vl.x, vl.y, hl, s * 9 + i);
+        const __half2 rh2 = f16::round_pair(vh.x, vh.y, hh, s * 9 + i);
+        uint2 w;
+        memcpy(&w.x, &rl2, 4);
+        memcpy(&w.y, &rh2, 4);
+        *reinterpret_cast<uint2 *>(o + (long long)i * plane) = w;
+      }
+      uint2 w;
+      memcpy(&w.x, &crl, 4);
+      memcpy(&w.y, &crh, 4);
+      *reinterpret_cast<uint2 *>(ro) = w;
+    } else {
+      // some nodes of the quad belong to the boundary kernel (or are
+      // solid): store the interior ones, each rounded as in the two-node
+      // kernel with zero in the lane of a node it does not store
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const float2 vl = f16::push2(i, gl[i], El[i], kl);
+        const float2 vh = f16::push2(i, gh[i], Eh[i], kh);
+        const __half2 rl2 = f16::round_pair(in0 ? vl.x : 0.0f, in1 ? vl.y : 0.0f,
+                                            hl, s * 9 + i);
+        const __half2 rh2 = f16::round_pair(in2 ? vh.x : 0.0f, in3 ? vh.y : 0.0f,
+                                            hh, s * 9 + i);
+        __half *oi = o + (long long)i * plane;
+        if (in0) oi[0] = __low2half(rl2);
+        if (in1) oi[1] = __high2half(rl2);
+        if (in2) oi[2] = __low2half(rh2);
+        if (in3) oi[3] = __high2half(rh2);
+      }
+      if (in0) ro[0] = __low2half(crl);
+      if (in1) ro[1] = __high2half(crl);
+      if (in2) ro[2] = __low2half(crh);
+      if (in3) ro[3] = __high2half(crh);
+    }
+  }
+}
+
 }  // namespace lbm
