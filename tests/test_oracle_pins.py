@@ -618,12 +618,11 @@ def test_pe_trend_single_fiber():
 # ---------------------------------------------------------------------------
 # p7: brute force -- an independent pull-form implementation on tiny domains
 # ---------------------------------------------------------------------------
-def _pull_step(gb, solid, kab, kbc, ux, uy, tau, cin, ns):
-    """Naive pull-form ADR step written from the rules, batched over the
-    first axis: gb[b, s, y, x, i] (pre-collision) -> next pre-collision."""
-    nb = gb.shape[0]
+def _collide(gb, solid, kab, kbc, ux, uy, tau, ns):
+    """BGK collision plus the link-wise source at every fluid node, batched
+    over the first axis: gb[b, s, y, x, i] (pre-collision) -> post-collision
+    g* (zero on solid nodes)."""
     ny, nx = solid.shape
-    out = np.zeros_like(gb)
     gs = np.zeros_like(gb)
     # collision + source at every fluid node
     for y in range(ny):
@@ -648,6 +647,15 @@ def _pull_step(gb, solid, kab, kbc, ux, uy, tau, cin, ns):
                     gs[:, 1, y, x, i] += ra - rb
                 if ns >= 3:
                     gs[:, 2, y, x, i] += rb
+    return gs
+
+
+def _pull_step(gb, solid, kab, kbc, ux, uy, tau, cin, ns):
+    """Naive pull-form ADR step written from the rules, batched over the
+    first axis: gb[b, s, y, x, i] (pre-collision) -> next pre-collision."""
+    ny, nx = solid.shape
+    gs = _collide(gb, solid, kab, kbc, ux, uy, tau, ns)
+    out = np.zeros_like(gb)
     # pull streaming with boundary rules
     for y in range(ny):
         for x in range(nx):
@@ -804,3 +812,78 @@ def test_adjoint_fiber_weight_gradient_matches_finite_differences():
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(fd) > 1e-6
         assert dw[f] == pytest.approx(fd, rel=1e-5)
+
+
+@pytest.mark.parametrize("ns", [2, 3])
+def test_adjoint_matches_dense_implicit_derivative(ns):
+    """p7 for the adjoint: d eps / d k at every solid node by dense linear
+    algebra, without the adjoint and without a difference step.  With the
+    flow frozen, one step is g' = M(k) g + b (the independent pull-form step
+    above); the source is linear in each rate, so M(k + e_n) g - M(k) g is
+    the exact k_n-derivative of the map at g.  The steady state solves
+    (I - M) g = b, so dg/dk_n = (I - M)^-1 (M(k + e_n) - M(k)) g.  The
+    outflux is the first moment of the post-collision state on x_p = nx - 3
+    (Sec. III.A.3), and eps of Eq. (A-B) is differentiated by a complex
+    step, exact for a rational function.  The oracle's adjoint, iterated to
+    convergence at that steady state, must give the same gradient."""
+    import scipy.linalg as sla
+
+    solid, kab, kbc, ux, uy, tau, cin = _tiny_case(ns)
+    ny, nx = solid.shape
+    xp = nx - 3
+    fluid = solid == 0
+    nfl = int(fluid.sum())
+    n = ns * nfl * 9
+
+    def flat(a):
+        return a[:, fluid, :].reshape(-1)
+
+    def full(v):
+        g = np.zeros((ns, ny, nx, 9), dtype=v.dtype)
+        g[:, fluid, :] = v.reshape(ns, nfl, 9)
+        return g
+
+    def step(g, ka, kb):
+        return flat(_pull_step(g[None], solid, ka, kb, ux, uy, tau, cin,
+                               ns)[0])
+
+    def outflux(g, ka, kb):
+        gs = _collide(g[None], solid, ka, kb, ux, uy, tau, ns)[0]
+        col = gs[:, fluid[:, xp], xp, :]            # [s, fluid rows, i]
+        return (col * CX).sum(axis=(1, 2)) / ny
+
+    def eps(nf):
+        return nf[ns - 1] / nf[:ns].sum()
+
+    basis = np.zeros((n + 1, ns, ny, nx, 9))
+    basis[1:, :, fluid, :] = np.eye(n).reshape(n, ns, nfl, 9)
+    img = _pull_step(basis, solid, kab, kbc, ux, uy, tau, cin, ns)
+    b = flat(img[0])
+    m = np.stack([flat(img[j + 1]) - b for j in range(n)], axis=1)
+    lu = sla.lu_factor(np.eye(n) - m)
+    g = full(sla.lu_solve(lu, b))
+    nf = outflux(g, kab, kbc)
+    assert np.abs(step(g, kab, kbc) - flat(g)).max() < 1e-13   # steady
+
+    prob = oracle.ADRProblem(solid, kab, kbc, ux, uy, tau, cin)
+    adj = oracle.adjoint(prob, g, 8000)
+    assert adj["eps"] == pytest.approx(eps(nf), rel=1e-12)
+
+    fields = [(kab, "dkab")] + ([(kbc, "dkbc")] if ns == 3 else [])
+    nonzero = 0
+    for y, x in zip(*np.nonzero(solid)):
+        for field, key in fields:
+            f2 = field.copy()
+            f2[y, x] += 1.0
+            ka = f2 if key == "dkab" else kab
+            kb = f2 if key == "dkbc" else kbc
+            dg = full(sla.lu_solve(lu, step(g, ka, kb) - step(g, kab, kbc)))
+            dn = outflux(dg, kab, kbc) + (outflux(g, ka, kb) - nf)
+            h = 1e-30
+            want = eps(nf + 1j * h * dn).imag / h
+            got = adj[key][y, x]
+            assert got == pytest.approx(want, rel=1e-11, abs=1e-15), (y, x, key)
+            nonzero += abs(want) > 1e-6
+        if ns == 2:
+            assert adj["dkbc"][y, x] == 0.0
+    assert nonzero >= 4
