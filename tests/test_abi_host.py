@@ -179,3 +179,66 @@ def test_set_periodic_status_and_stale_upload(lib):
     s, a, _ = g.fields()
     so, ao, _ = oracle.raster(16, 8, [[8.0, 4.0, 2.0, 1, 0, -1]], 0.1, 0.0)
     assert np.array_equal(s, so) and np.array_equal(a, ao)
+
+
+def test_batch_and_particle_argument_errors(lib):
+    """The batch, particle-tracking and outflux entry points check their
+    arguments on the host before any device work: each refusal is a status
+    code with a message, and the workspace queries return 0 for what the
+    create calls would refuse."""
+    g = lbm.Geometry(40, 16, np.array([[20.0, 8.0, 3.0, 1, 0, -1]]), 0.1, 0.0)
+    geoms = (ctypes.c_void_p * 2)(g.handle.value, g.handle.value)
+    prm = (lbm.lbm_adr_params * 2)(lbm.adr_params(3, 0.8),
+                                   lbm.adr_params(3, 0.8))
+    us = (ctypes.c_void_p * 2)(256, 512)
+    ws = ctypes.c_void_p(4096)
+    out = ctypes.c_void_p()
+    # geometries that were never uploaded
+    assert lib.lbm_batch_ws_bytes(2, geoms, prm) == 0
+    st = lib.lbm_batch_create(2, geoms, prm, us, ws, 1 << 20,
+                              ctypes.byref(out))
+    assert st == lbm.LBM_EINVAL and b"uploaded" in lib.lbm_last_error()
+    assert out.value is None
+    assert lib.lbm_batch_create(0, geoms, prm, us, ws, 1 << 20,
+                                ctypes.byref(out)) == lbm.LBM_EINVAL
+    assert lib.lbm_batch_create(2, geoms, prm, us, ws, 1 << 20,
+                                None) == lbm.LBM_EINVAL
+    assert b"out is NULL" in lib.lbm_last_error()
+
+    # particle tracking: workspace size grows with capacity and fibers
+    assert lib.lbm_rwpt_ws_bytes(0, 1) == 0
+    assert lib.lbm_rwpt_ws_bytes(10, -1) == 0
+    s1 = lib.lbm_rwpt_ws_bytes(1000, 2)
+    assert s1 > 0
+    assert lib.lbm_rwpt_ws_bytes(2000, 2) > s1
+    assert lib.lbm_rwpt_ws_bytes(1000, 20) > s1
+    fib = np.array([[20.0, 8.0, 3.0, 1, 0, -1]])
+    fp = fib.ctypes.data_as(ctypes.c_void_p)
+
+    def create(nx=40, ny=16, k1=0.1, k2=0.0, capacity=1000, wsp=ws,
+               nbytes=1 << 20, **kw):
+        p = lbm.lbm_rwpt_params(D=kw.get("D", 0.1), dt=kw.get("dt", 0.5),
+                                delta=0.2, density=1.0, radius_offset=0.5,
+                                seed=1, nspecies=kw.get("nspecies", 2),
+                                flags=kw.get("flags", 0))
+        h = ctypes.c_void_p()
+        return lib.lbm_rwpt_create(nx, ny, fp, 1, k1, k2, ctypes.byref(p),
+                                   None, capacity, wsp, nbytes,
+                                   ctypes.byref(h))
+
+    assert create(nx=1) == lbm.LBM_EINVAL
+    assert create(capacity=0) == lbm.LBM_EINVAL
+    assert create(dt=0.0) == lbm.LBM_EINVAL
+    assert create(nspecies=4) == lbm.LBM_EINVAL
+    assert create(k1=3.0) == lbm.LBM_EINVAL          # k dt > 1
+    assert b"k dt" in lib.lbm_last_error()
+    assert create(flags=1 << 4) == lbm.LBM_EINVAL    # unknown flag bit
+    assert create(wsp=ctypes.c_void_p(4096 + 16)) == lbm.LBM_EINVAL
+    assert b"aligned" in lib.lbm_last_error()
+    assert create(nbytes=16) == lbm.LBM_ENOMEM
+    assert b"too small" in lib.lbm_last_error()
+
+    # outflux without workspace: NULL solver or output
+    flux = (ctypes.c_double * 3)()
+    assert lib.lbm_adr_outflux_noalloc(None, -1, None, flux) == lbm.LBM_EINVAL
+    assert b"NULL" in lib.lbm_last_error()
