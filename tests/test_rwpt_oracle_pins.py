@@ -127,3 +127,51 @@ def test_particles_stay_outside_fibers_and_walls():
         for cx, cy, r, *_ in fib:
             assert (np.hypot(x - cx, y - cy) >= r + 0.5 - 1e-12).all()
     assert sim.out.sum() > 0 and (sim.p.s > 0).any()
+
+
+@pytest.mark.parametrize("cat", [1, 2, 3])
+def test_reactive_shell_with_particles_at_rest(cat):
+    """Step 4 of Sec. III.B with D = 0 and no flow, so particles stay where
+    the fill put them: a particle reacts only inside the shell
+    r <= d < r + delta around the fiber, r = R + 1/2 (reading R24), only
+    for the species the catalyst acts on (A on an A->B fiber; nothing for
+    A on a B->C fiber; A only on the k1 half of a side-by-side fiber, where
+    (p - c).(cos t, sin t) >= 0), and there with probability k dt per step:
+    the shell's A fraction after n steps is (1 - k dt)^n (binomial error).
+    Particles outside it never change species."""
+    nx = ny = 40
+    R, delta, k, dt, th = 6.0, 0.8, 0.6, 0.5, 0.9
+    fib = np.array([[20.3, 19.6, R, cat, th, -1]])
+    sim = rwpt.RWPT(nx, ny, fib, k, k, None, 0.0, dt=dt, delta=delta,
+                    density=200.0, periodic=True, nspecies=2,
+                    seed=17).init()
+    x0, y0, s0, id0 = sim.p.sorted()
+    assert (s0 == 0).all()
+    dx, dy = x0 - fib[0, 0], y0 - fib[0, 1]
+    d = np.hypot(dx, dy)
+    r = R + 0.5
+    shell = (d >= r) & (d < r + delta)
+    if cat == 2:
+        active = np.zeros_like(shell)
+    elif cat == 3:
+        active = shell & (dx * math.cos(th) + dy * math.sin(th) >= 0.0)
+    else:
+        active = shell
+    # the fill covers the shell at the density (Poisson count)
+    area = math.pi * ((r + delta) ** 2 - r ** 2)
+    assert abs(shell.sum() - 200.0 * area) < 5 * math.sqrt(200.0 * area)
+    for n in (1, 3):
+        while sim.t < n:
+            sim.step()
+        x, y, s, ids = sim.p.sorted()
+        assert np.array_equal(ids, id0)
+        assert np.array_equal(x, x0) and np.array_equal(y, y0)
+        assert (s[~active] == 0).all()
+        if active.any():
+            m = int(active.sum())
+            p = (1 - k * dt) ** n
+            frac = (s[active] == 0).mean()
+            assert abs(frac - p) < 5 * math.sqrt(p * (1 - p) / m)
+            assert (s[active] <= 1).all()          # B does not react on
+    if cat == 3:
+        assert active.sum() > 0.3 * shell.sum()     # about half the shell
