@@ -887,3 +887,32 @@ def test_adjoint_matches_dense_implicit_derivative(ns):
         if ns == 2:
             assert adj["dkbc"][y, x] == 0.0
     assert nonzero >= 4
+
+
+# ---------------------------------------------------------------------------
+# Eq. (BC): the inlet's anti-bounce-back imposes its concentration
+# ---------------------------------------------------------------------------
+def test_inlet_anti_bounce_back_fixes_the_concentration_without_flow():
+    """Sec. III.A.3, Eq. (BC): with u = 0 and no reaction, the anti-bounce-
+    back inlet (incoming g_i = -g*_opp + 2 w_i C_w) is a Dirichlet condition,
+    the outlet's (C_w = C of the boundary node) a zero-gradient one, and the
+    walls and the inert fiber bounce back: from C = 0 everywhere the lattice
+    must fill up to C = C_w at every fluid node.  A stays the only species
+    the default inlet feeds; with every species on anti-bounce-back (test
+    mode) B and C fill up to their own inlet values."""
+    nx, ny = 14, 7
+    solid, kab, kbc = oracle.raster(nx, ny, [[7.2, 3.3, 1.6, 0, 0, -1]],
+                                    0.0, 0.0)
+    assert solid.sum() > 0
+    z = np.zeros((ny, nx))
+    fl = solid == 0
+    for flags, cin, want in ((0, [1.0, 0.4, 0.9], [1.0, 0.0, 0.0]),
+                             (oracle.INLET_ABB_ALL, [1.0, 0.3, 0.7],
+                              [1.0, 0.3, 0.7])):
+        prob = oracle.ADRProblem(solid, kab, kbc, z, z, [1.0, 0.8, 1.3], cin,
+                                 flags=flags)
+        g = prob.init(np.zeros((3, ny, nx)))
+        prob.steps(g, 40000)
+        c = prob.conc(g)
+        for s in range(3):
+            assert np.abs(c[s][fl] - want[s]).max() < 1e-10, (flags, s)
