@@ -916,3 +916,73 @@ def test_inlet_anti_bounce_back_fixes_the_concentration_without_flow():
         c = prob.conc(g)
         for s in range(3):
             assert np.abs(c[s][fl] - want[s]).max() < 1e-10, (flags, s)
+
+
+# ---------------------------------------------------------------------------
+# p7 for the flow lattice: an independent pull-form flow step on a tiny domain
+# ---------------------------------------------------------------------------
+def _flow_pull_step(f, solid, tau, u0):
+    """One D2Q9 BGK flow step written from the rules (reading R1): BGK at
+    every fluid node; pull streaming; halfway bounce-back from walls and
+    solid nodes; at the inlet velocity bounce-back, f_i = f*_opp + 6 w_i
+    rho_w c_i.u_w with rho_w = 1 and u_w = (u_in(y), 0) of the node's row;
+    at the outlet pressure anti-bounce-back, f_i = -f*_opp + 2 w_i rho_w
+    (1 + 4.5 (c_i.u_w)^2 - 1.5 u_w^2) with rho_w = 1 and u_w the node's own
+    velocity at time t; the x-edge rule wins on corner links (R7)."""
+    ny, nx = solid.shape
+    fs = np.zeros_like(f)
+    ux = np.zeros((ny, nx))
+    uy = np.zeros((ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            if solid[y, x]:
+                continue
+            fi = f[y, x]
+            rho = fi.sum()
+            ux[y, x] = (fi * CX).sum() / rho
+            uy[y, x] = (fi * CY).sum() / rho
+            cu = CX * ux[y, x] + CY * uy[y, x]
+            uu = ux[y, x] ** 2 + uy[y, x] ** 2
+            feq = W * rho * (1 + 3 * cu + 4.5 * cu ** 2 - 1.5 * uu)
+            fs[y, x] = fi - (fi - feq) / tau
+    out = np.zeros_like(f)
+    for y in range(ny):
+        for x in range(nx):
+            if solid[y, x]:
+                continue
+            for i in range(9):
+                sx, sy = x - CX[i], y - CY[i]
+                o = OPP[i]
+                if sx < 0:
+                    uin = 4 * u0 * (y + 0.5) * (ny - 0.5 - y) / ny ** 2
+                    v = fs[y, x, o] + 6 * W[i] * CX[i] * uin
+                elif sx >= nx:
+                    cu = CX[i] * ux[y, x] + CY[i] * uy[y, x]
+                    uu = ux[y, x] ** 2 + uy[y, x] ** 2
+                    v = -fs[y, x, o] + 2 * W[i] * (1 + 4.5 * cu ** 2
+                                                   - 1.5 * uu)
+                elif sy < 0 or sy >= ny or solid[sy, sx]:
+                    v = fs[y, x, o]
+                else:
+                    v = fs[sy, sx, i]
+                out[y, x, i] = v
+    return out
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.3])
+def test_flow_step_matches_independent_pull_implementation(tau):
+    """Every flow link type (inlet and outlet with their corners, walls, a
+    fiber, a fiber touching a wall, plain fluid) on an 11x7 lattice: one
+    oracle flow step equals the naive pull-form step on random states near
+    equilibrium (1e-14)."""
+    nx, ny, u0 = 11, 7, 0.05
+    solid, _, _ = oracle.raster(nx, ny, [[4.3, 3.2, 1.4, 0, 0, -1],
+                                         [8.0, 1.0, 1.0, 0, 0, -1]], 0, 0)
+    assert solid[0].any() and solid.sum() >= 8
+    fl = solid == 0
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        f = W * (1 + 0.3 * (rng.random((ny, nx, 9)) - 0.5)) * fl[:, :, None]
+        want = _flow_pull_step(f, solid, tau, u0)
+        got = oracle.flow_steps(f.copy(), solid, tau, u0, 1)
+        assert np.abs(got[fl] - want[fl]).max() < 1e-14
