@@ -986,3 +986,33 @@ def test_flow_step_matches_independent_pull_implementation(tau):
         want = _flow_pull_step(f, solid, tau, u0)
         got = oracle.flow_steps(f.copy(), solid, tau, u0, 1)
         assert np.abs(got[fl] - want[fl]).max() < 1e-14
+
+
+def test_initial_states_have_the_prescribed_moments():
+    """Reading R13: the flow starts at equilibrium with rho = 1 and
+    u = (u_in(y), 0) on every fluid node (zero on solid nodes); an ADR
+    species starts at the second-order equilibrium of (C, u), whose zeroth,
+    first and second moments are C, C u and C (I/3 + u u) exactly."""
+    nx, ny, u0 = 13, 9, 0.05
+    solid, _, _ = oracle.raster(nx, ny, [[6.2, 4.1, 2.0, 0, 0, -1]], 0, 0)
+    fl = solid == 0
+    f = oracle.flow_init_channel(solid, u0)
+    rho, ux, uy = oracle.flow_moments(f, solid)
+    yy = np.arange(ny)[:, None] * np.ones((1, nx))
+    uin = 4 * u0 * (yy + 0.5) * (ny - 0.5 - yy) / ny ** 2
+    assert np.abs(rho[fl] - 1).max() < 1e-15
+    assert np.abs(ux[fl] - uin[fl]).max() < 1e-16
+    assert np.abs(uy[fl]).max() < 1e-17
+    assert not f[~fl].any()
+    rng = np.random.default_rng(9)
+    vx = 0.08 * (rng.random((ny, nx)) - 0.5) * fl
+    vy = 0.08 * (rng.random((ny, nx)) - 0.5) * fl
+    c0 = rng.random((3, ny, nx)) * fl
+    g = oracle.adr_init(solid, vx, vy, c0)
+    assert np.abs(g.sum(axis=3) - c0).max() < 1e-15
+    assert np.abs((g * CX).sum(axis=3) - c0 * vx).max() < 1e-16
+    assert np.abs((g * CY).sum(axis=3) - c0 * vy).max() < 1e-16
+    # second moments of the D2Q9 equilibrium: C (I/3 + u u)
+    assert np.abs((g * CX * CX).sum(axis=3) - c0 * (1 / 3 + vx * vx)).max() < 1e-15
+    assert np.abs((g * CX * CY).sum(axis=3) - c0 * vx * vy).max() < 1e-16
+    assert np.abs((g * CY * CY).sum(axis=3) - c0 * (1 / 3 + vy * vy)).max() < 1e-15
