@@ -28,9 +28,10 @@ passage of the paper (Sitaru & Gekle, arXiv 2109.04455):
                         steady-state criterion; this is the reading used).
 
 Pinned by ``tests/test_oracle_pins.py`` (closed forms, exact moment
-recurrences, conservation invariants, a dense one-step matrix built by an
-independent pull-form implementation on tiny domains, the paper's worked
-Da/k numbers).  The channel ADR efficiency of the full configurations has no
+recurrences, conservation invariants, independent pull-form flow and ADR
+steps on tiny domains, the dense one-step matrix built from the latter with
+its steady solve and, by implicit differentiation, the exact rate gradient
+the adjoint must reproduce, the paper's worked Da/k numbers).  The channel ADR efficiency of the full configurations has no
 printed value in the paper: parity there is pinned only through those
 invariants.
 """
