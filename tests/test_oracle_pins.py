@@ -615,6 +615,31 @@ def test_pe_trend_single_fiber():
     assert eps[0] > eps[1] > eps[2] > 0
 
 
+def test_da_trend_single_fiber():
+    """Sec. IV.A: at fixed Pe the efficiency rises with Da (a faster surface
+    reaction), in proportion to Da while the reaction limits the rate, and
+    saturating once diffusion to the surface does (the shape of the paper's
+    efficiency-against-Da figure)."""
+    nx, ny, r, pe = 96, 48, 5.0, 5.0
+    solid, kab, kbc = oracle.raster(nx, ny, [[30.0, 24.0, r, 1, 0, -1]], 1, 0)
+    _, ux, uy, _ = oracle.flow_run(solid, 0.8, 0.05, 3000)
+    d = inputs.diffusivity_from_pe(0.05, r, pe)
+    tau = inputs.tau_from_diffusivity(d)
+    eps = []
+    das = (0.01, 0.1, 30.0, 300.0)
+    for da in das:
+        k = inputs.rate_from_da(da, d, r)
+        assert k < 1.0
+        p = oracle.ADRProblem(solid, kab * k, kbc, ux, uy, [tau, tau],
+                              [1, 0])
+        eps.append(p.run(3000)["eps"])
+    assert 0 < eps[0] < eps[1] < eps[2] < eps[3]
+    # reaction-limited: ten times the rate gives nearly ten times eps
+    assert 9.0 < eps[1] / eps[0] < 10.0
+    # diffusion-limited: ten times the rate gives much less than that
+    assert eps[3] / eps[2] < 2.5
+
+
 # ---------------------------------------------------------------------------
 # p7: brute force -- an independent pull-form implementation on tiny domains
 # ---------------------------------------------------------------------------
